@@ -1,0 +1,239 @@
+"""Seeded synthetic graph inputs: R-MAT and SBM edge lists, labels, weights.
+
+This module only draws random inputs; it holds none of the embedding's
+arithmetic.  It is the one piece of code that both the oracle side and the GPU
+side of the test suite consume.
+
+Every random number comes from the counter-based generator Philox4x32-10
+(Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+SC'11), so any single edge, label or weight is a pure function of
+(seed, index).  The host implementation here (numpy) and the device
+implementation in ``graphgen.cu`` compute the same values bit for bit; a test
+checks that on samples.  Large graphs are drawn on the device; small ones on
+the host.
+
+Counter layout of one Philox call: (index_lo, index_hi, word2, tag) with the
+64-bit seed as key.  ``tag`` separates the streams below.
+
+R-MAT (Chakrabarti, Zhan, Faloutsos, SDM'04): each edge picks one quadrant per
+level with probabilities (a, b, c, 1-a-b-c) using 16-bit uniforms
+(thresholds round(p * 65536)), most significant bit first; node ids are then
+mapped through a keyed bijection of [0, 2^scale) (Graph500-style relabeling,
+so that hubs are not clustered at small ids).  When n < 2^scale an edge with
+an endpoint >= n is redrawn with the next attempt number (word2 carries
+attempt * 8 + call); after 64 attempts the endpoints are reduced modulo n.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASK32 = np.uint64(0xFFFFFFFF)
+_M0 = np.uint64(0xD2511F53)
+_M1 = np.uint64(0xCD9E8D57)
+_W0 = np.uint64(0x9E3779B9)
+_W1 = np.uint64(0xBB67AE85)
+
+TAG_RMAT = 0x524D4154     # "RMAT"
+TAG_PERM = 0x5045524D     # "PERM"
+TAG_LABEL = 0x4C41424C    # "LABL"
+TAG_WEIGHT = 0x57474854   # "WGHT"
+TAG_SBM = 0x53424D30      # "SBM0"
+TAG_SHUFFLE = 0x53484646  # "SHFF"
+
+RMAT_MAX_ATTEMPTS = 64
+# odd multipliers of the id bijection (any odd constants work)
+_PERM_MUL1 = 0x2545F491
+_PERM_MUL2 = 0x9E3779B1
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds on numpy arrays (broadcast).  Returns four
+    uint32 arrays."""
+    c0, c1, c2, c3 = (np.asarray(x, dtype=np.uint64) & MASK32
+                      for x in np.broadcast_arrays(c0, c1, c2, c3))
+    k0 = np.uint64(int(k0) & 0xFFFFFFFF)
+    k1 = np.uint64(int(k1) & 0xFFFFFFFF)
+    for r in range(10):
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & MASK32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        if r != 9:
+            k0 = (k0 + _W0) & MASK32
+            k1 = (k1 + _W1) & MASK32
+    return tuple(x.astype(np.uint32) for x in (c0, c1, c2, c3))
+
+
+def _key(seed):
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return seed & 0xFFFFFFFF, seed >> 32
+
+
+def _words(idx, word2, tag, seed):
+    idx = np.asarray(idx, dtype=np.uint64)
+    k0, k1 = _key(seed)
+    return philox4x32_10(idx & MASK32, idx >> np.uint64(32), word2, tag, k0, k1)
+
+
+# ----------------------------------------------------------------------------
+# R-MAT
+# ----------------------------------------------------------------------------
+def rmat_thresholds(a, b, c):
+    A = int(round(a * 65536))
+    AB = int(round((a + b) * 65536))
+    ABC = int(round((a + b + c) * 65536))
+    if not (0 <= A <= AB <= ABC <= 65536):
+        raise ValueError("R-MAT probabilities must be non-negative and sum <= 1")
+    return A, AB, ABC
+
+
+def perm_keys(seed):
+    w = _words(np.zeros(1, np.uint64), 0, TAG_PERM, seed)
+    return int(w[0][0]), int(w[1][0])
+
+
+def permute_ids(x, scale, seed):
+    """Keyed bijection of [0, 2^scale): xor, multiply by odd, xorshift, twice."""
+    mask = np.uint64((1 << scale) - 1)
+    h = np.uint64(max(1, scale // 2))
+    ka, kb = perm_keys(seed)
+    x = np.asarray(x, dtype=np.uint64)
+    x = (x ^ np.uint64(ka)) & mask
+    x = (x * np.uint64(_PERM_MUL1)) & mask
+    x ^= x >> h
+    x = (x * np.uint64(_PERM_MUL2)) & mask
+    x ^= x >> h
+    x = (x ^ np.uint64(kb)) & mask
+    return x
+
+
+def _rmat_attempt(idx, attempt, scale, thr, seed):
+    A, AB, ABC = (np.uint32(t) for t in thr)
+    u = np.zeros(idx.shape, np.uint64)
+    v = np.zeros(idx.shape, np.uint64)
+    ncalls = (scale + 7) // 8
+    for call in range(ncalls):
+        w = _words(idx, attempt * 8 + call, TAG_RMAT, seed)
+        for j in range(8):
+            level = call * 8 + j
+            if level >= scale:
+                break
+            r = (w[j // 2] >> np.uint32(16 * (j % 2))) & np.uint32(0xFFFF)
+            ub = (r >= AB).astype(np.uint64)          # quadrants c, d: row bit 1
+            vb = (((r >= A) & (r < AB)) | (r >= ABC)).astype(np.uint64)
+            u = (u << np.uint64(1)) | ub
+            v = (v << np.uint64(1)) | vb
+    return permute_ids(u, scale, seed), permute_ids(v, scale, seed)
+
+
+def rmat_edges(scale, n, start, count, seed, a=0.57, b=0.19, c=0.19):
+    """Edges [start, start+count) of the seeded R-MAT graph, (count, 2) int32."""
+    if n > (1 << scale) or n < 1:
+        raise ValueError("need 1 <= n <= 2^scale")
+    thr = rmat_thresholds(a, b, c)
+    idx = np.arange(start, start + count, dtype=np.uint64)
+    out_u = np.zeros(count, np.uint64)
+    out_v = np.zeros(count, np.uint64)
+    todo = np.arange(count)
+    nn = np.uint64(n)
+    for attempt in range(RMAT_MAX_ATTEMPTS):
+        if todo.size == 0:
+            break
+        u, v = _rmat_attempt(idx[todo], attempt, scale, thr, seed)
+        ok = (u < nn) & (v < nn)
+        out_u[todo[ok]] = u[ok]
+        out_v[todo[ok]] = v[ok]
+        if attempt == RMAT_MAX_ATTEMPTS - 1:
+            bad = todo[~ok]
+            out_u[bad] = u[~ok] % nn
+            out_v[bad] = v[~ok] % nn
+        todo = todo[~ok]
+    return np.stack([out_u, out_v], axis=1).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# labels and weights
+# ----------------------------------------------------------------------------
+def unlabeled_threshold(frac_unlabeled):
+    return min(int(frac_unlabeled * 4294967296.0), 4294967296)
+
+
+def labels(n, K, seed, frac_unlabeled=0.0, start=0):
+    """Y[i] uniform in [0, K), or -1 with probability frac_unlabeled."""
+    idx = np.arange(start, start + n, dtype=np.uint64)
+    w = _words(idx, 0, TAG_LABEL, seed)
+    cls = ((w[1].astype(np.uint64) * np.uint64(K)) >> np.uint64(32)).astype(np.int32)
+    thr = unlabeled_threshold(frac_unlabeled)
+    if thr > 0:
+        cls[w[0].astype(np.uint64) < np.uint64(thr)] = -1
+    return cls
+
+
+def weights(s, seed, start=0):
+    """w[i] = (top 24 bits + 1) / 2^24, uniform on (0, 1], exact in float32."""
+    idx = np.arange(start, start + s, dtype=np.uint64)
+    w = _words(idx, 0, TAG_WEIGHT, seed)
+    return (((w[0] >> np.uint32(8)).astype(np.float64) + 1.0) / 16777216.0
+            ).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# stochastic block model (host only; small graphs)
+# ----------------------------------------------------------------------------
+def sbm(block_sizes, p_in, p_out, seed, shuffle=True):
+    """Undirected SBM without self-loops: every pair u < v is an edge with
+    probability p_in (same block) or p_out.  Returns (edges (s,2) int32,
+    block labels int32).  Pair (u, v) in block pair (i, j) uses Philox word
+    (t mod 4) of call t // 4, t the pair's index in the block rectangle."""
+    sizes = [int(x) for x in block_sizes]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    nb = len(sizes)
+    chunks = []
+    for i in range(nb):
+        for j in range(i, nb):
+            p = p_in if i == j else p_out
+            thr = np.uint64(min(int(p * 4294967296.0), 4294967295))
+            mi, mj = sizes[i], sizes[j]
+            total = mi * mj
+            ncalls = (total + 3) // 4
+            step = 1 << 21
+            for c0 in range(0, ncalls, step):
+                calls = np.arange(c0, min(ncalls, c0 + step), dtype=np.uint64)
+                words = _words(calls, i * nb + j, TAG_SBM, seed)
+                r = np.stack(words, axis=1).ravel()   # trial t = 4*call + word
+                t = np.uint64(4 * c0) + np.flatnonzero(r < np.uint32(thr)
+                                                       ).astype(np.uint64)
+                hit = t[t < np.uint64(total)]
+                a = (hit // np.uint64(mj)).astype(np.int64)
+                b = (hit % np.uint64(mj)).astype(np.int64)
+                if i == j:
+                    keep = a < b
+                    a, b = a[keep], b[keep]
+                chunks.append(np.stack([a + offs[i], b + offs[j]], axis=1))
+    e = (np.concatenate(chunks) if chunks else np.zeros((0, 2), np.int64))
+    e = e.astype(np.int32)
+    if shuffle and e.shape[0] > 1:
+        key = _words(np.arange(e.shape[0], dtype=np.uint64), 0, TAG_SHUFFLE, seed)
+        order = np.argsort((key[0].astype(np.uint64) << np.uint64(32))
+                           | key[1].astype(np.uint64), kind="stable")
+        e = e[order]
+    y = np.repeat(np.arange(nb, dtype=np.int32), sizes)
+    return np.ascontiguousarray(e), y
+
+
+def tiny_sbm(seed=1):
+    """The 5-block SBM of the small parity workload: 5 x 2000 nodes,
+    p_in = 0.02, p_out = 0.002, labels = blocks, K = 5."""
+    return sbm([2000] * 5, 0.02, 0.002, seed)
+
+
+def random_graph(n, s, seed, self_loops=True):
+    """Uniform random multigraph with s edges on n nodes (small tests)."""
+    idx = np.arange(s, dtype=np.uint64)
+    w = _words(idx, 0, TAG_RMAT ^ 0xFF, seed)
+    u = ((w[0].astype(np.uint64) * np.uint64(n)) >> np.uint64(32)).astype(np.int64)
+    v = ((w[1].astype(np.uint64) * np.uint64(n)) >> np.uint64(32)).astype(np.int64)
+    if not self_loops:
+        v = np.where(u == v, (v + 1) % max(n, 1), v)
+    return np.stack([u, v], axis=1).astype(np.int32)

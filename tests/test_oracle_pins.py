@@ -1,0 +1,278 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: every expected value comes from
+a hand derivation (tests/golden), a different formulation (dense product,
+pairwise exact rationals, scipy's normalised Laplacian), an invariant or a
+statistical expectation.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import _pins
+
+
+def _case_arrays(case):
+    edges = np.asarray(case["edges"], dtype=np.int32).reshape(-1, 2)
+    w = None if case["weights"] is None else np.asarray(case["weights"], np.float32)
+    return edges, w, np.asarray(case["Y"], dtype=np.int32)
+
+
+@pytest.mark.parametrize("case", _pins.load_hand_cases(), ids=lambda c: c["name"])
+def test_hand_cases(case):
+    edges, w, Y = _case_arrays(case)
+    Z = oracle.embed(edges, Y, case["K"], weights=w, laplacian=case["laplacian"])
+    expect = np.array([[_pins.parse_exact(x) for x in row] for row in case["Z"]])
+    assert Z.shape == expect.shape
+    np.testing.assert_allclose(Z, expect, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize(
+    "case", [c for c in _pins.load_hand_cases()
+             if c["weights"] is None and not c["laplacian"]],
+    ids=lambda c: c["name"])
+def test_hand_cases_exact_counts(case):
+    edges, _, Y = _case_arrays(case)
+    C = oracle.counts(edges, Y, case["K"])
+    nk = [int((Y == k).sum()) for k in range(case["K"])]
+    for u, row in enumerate(case["Z"]):
+        for k, text in enumerate(row):
+            got = Fraction(int(C[u, k]), nk[k]) if nk[k] else Fraction(int(C[u, k]))
+            assert got == _pins.parse_fraction(text), (u, k)
+
+
+def _random_case(seed, n, s, K, frac_unlabeled, weighted):
+    edges = graphgen.random_graph(n, s, seed)
+    Y = graphgen.labels(n, K, seed + 1, frac_unlabeled)
+    w = graphgen.weights(s, seed + 2) if weighted else None
+    return edges, Y, w
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("weighted", [False, True])
+def test_dense_closed_form(seed, weighted):
+    n, s, K = 37 + 5 * seed, 150 + 40 * seed, 1 + seed % 5
+    edges, Y, w = _random_case(100 + seed, n, s, K, 0.2, weighted)
+    Z = oracle.embed(edges, Y, K, weights=w)
+    Zd = _pins.dense_embedding(edges, Y, K, weights=w)
+    np.testing.assert_allclose(Z, Zd, rtol=1e-12, atol=1e-13)
+
+
+def test_exhaustive_three_node_graphs():
+    """Every edge set on 3 nodes (self-loops included) under every labelling
+    with classes {-1, 0, 1}, both edge orientations: exact rationals."""
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    rng = np.random.default_rng(0)
+    for mask in range(1 << len(pairs)):
+        chosen = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        for Yt in itertools.product([-1, 0, 1], repeat=3):
+            # orient each edge randomly: the result must not depend on it
+            edges = [(v, u) if rng.random() < 0.5 else (u, v) for u, v in chosen]
+            e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+            Y = np.asarray(Yt, dtype=np.int32)
+            C = oracle.counts(e, Y, 2)
+            Z = oracle.embed(e, Y, 2)
+            exact = _pins.pairwise_exact(edges, list(Yt), 2)
+            nk = [Yt.count(0), Yt.count(1)]
+            for u in range(3):
+                for k in range(2):
+                    q = exact[u][k]
+                    assert Fraction(int(C[u, k]), nk[k] or 1) == q
+                    assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_row_and_column_sum_invariants(seed):
+    n, s, K = 300, 2000, 6
+    edges, Y, w = _random_case(200 + seed, n, s, K, 0.15, True)
+    Z = oracle.embed(edges, Y, K, weights=w)
+    nk = np.bincount(Y[Y >= 0], minlength=K).astype(np.float64)
+    u, v = edges[:, 0].astype(np.int64), edges[:, 1].astype(np.int64)
+    w64 = w.astype(np.float64)
+    # R1: sum_k n_k Z[u,k] = weight of u's edges whose other end is labelled
+    lab_v = (Y[v] >= 0).astype(np.float64)
+    lab_u = (Y[u] >= 0).astype(np.float64)
+    r1 = np.bincount(u, w64 * lab_v, n) + np.bincount(v, w64 * lab_u, n)
+    np.testing.assert_allclose(Z @ nk, r1, rtol=1e-12, atol=1e-12)
+    # R2: sum_u n_k Z[u,k] = total weighted degree of the nodes of class k
+    d = np.bincount(u, w64, n) + np.bincount(v, w64, n)
+    r2 = np.array([d[Y == k].sum() for k in range(K)])
+    np.testing.assert_allclose(Z.sum(axis=0) * nk, r2, rtol=1e-12, atol=1e-12)
+
+
+def test_single_class_is_degree_over_n():
+    n, s = 500, 4000
+    edges, _, w = _random_case(7, n, s, 1, 0.0, True)
+    Y = np.zeros(n, np.int32)
+    Z = oracle.embed(edges, Y, 1, weights=w)
+    u, v = edges[:, 0].astype(np.int64), edges[:, 1].astype(np.int64)
+    d = np.bincount(u, w.astype(np.float64), n) + np.bincount(v, w.astype(np.float64), n)
+    np.testing.assert_allclose(Z[:, 0], d / n, rtol=1e-12, atol=1e-15)
+
+
+def test_equivariance():
+    n, s, K = 200, 1500, 5
+    edges, Y, w = _random_case(11, n, s, K, 0.1, True)
+    Z = oracle.embed(edges, Y, K, weights=w)
+    C = oracle.counts(edges, Y, K)
+    rng = np.random.default_rng(3)
+    # edge order and orientation
+    order = rng.permutation(s)
+    flip = rng.random(s) < 0.5
+    e2 = edges[order].copy()
+    e2[flip] = e2[flip][:, ::-1]
+    np.testing.assert_allclose(oracle.embed(e2, Y, K, weights=w[order]), Z,
+                               rtol=1e-12, atol=1e-15)
+    assert np.array_equal(oracle.counts(e2, Y, K), C)
+    # class ids permuted -> columns permuted
+    cp = rng.permutation(K)
+    Y2 = np.where(Y >= 0, cp[np.maximum(Y, 0)], -1).astype(np.int32)
+    Zc = oracle.embed(edges, Y2, K, weights=w)
+    np.testing.assert_allclose(Zc[:, cp], Z, rtol=1e-12, atol=1e-15)
+    # node ids permuted -> rows permuted
+    p = rng.permutation(n).astype(np.int32)
+    e3 = p[edges]
+    Y3 = np.empty_like(Y)
+    Y3[p] = Y
+    Zn = oracle.embed(e3, Y3, K, weights=w)
+    np.testing.assert_allclose(Zn[p], Z, rtol=1e-12, atol=1e-15)
+    assert np.array_equal(oracle.counts(e3, Y3, K)[p], C)
+
+
+def test_sbm_block_means(tiny_sbm_graph):
+    """Tiny SBM: Z[u,k] = (neighbours of u in block k) / 2000, so block means
+    are p_in (2000-1)/2000 on the diagonal and p_out off it."""
+    edges, Y = tiny_sbm_graph
+    K, m = 5, 2000
+    n_pairs = 5 * m * (m - 1) // 2 + 10 * m * m
+    mean_s = 5 * m * (m - 1) / 2 * 0.02 + 10 * m * m * 0.002
+    var_s = 5 * m * (m - 1) / 2 * 0.02 * 0.98 + 10 * m * m * 0.002 * 0.998
+    assert abs(edges.shape[0] - mean_s) < 5 * np.sqrt(var_s), n_pairs
+    Z = oracle.embed(edges, Y, K)
+    for b in range(K):
+        rows = Z[Y == b]
+        for k in range(K):
+            if k == b:
+                p, cnt = 0.02, m - 1
+            else:
+                p, cnt = 0.002, m
+            mean = p * cnt / m
+            sigma = np.sqrt(cnt * p * (1 - p)) / m / np.sqrt(m)
+            assert abs(rows[:, k].mean() - mean) < 5 * sigma, (b, k)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("weighted", [False, True])
+def test_laplacian_matches_scipy_normalised_laplacian(seed, weighted):
+    """Laplacian reading vs scipy: D^-1/2 A D^-1/2 = I - L_normed on nodes with
+    positive degree (graphs without self-loops, since scipy ignores the
+    diagonal of A)."""
+    scipy_csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    n, s, K = 60 + 7 * seed, 200 + 30 * seed, 3 + seed
+    edges = graphgen.random_graph(n, s, 300 + seed, self_loops=False)
+    Y = graphgen.labels(n, K, 301 + seed, 0.2)
+    w = graphgen.weights(s, 302 + seed) if weighted else None
+    Z = oracle.embed(edges, Y, K, weights=w, laplacian=True)
+    A = _pins.dense_adjacency(edges, n, w)
+    L = scipy_csgraph.laplacian(A, normed=True)
+    S = np.eye(n) - L
+    deg = A.sum(axis=1)
+    live = deg > 0
+    S[~live, :] = 0.0
+    expect = S @ _pins.dense_projection(Y, K)
+    np.testing.assert_allclose(Z[live], expect[live], rtol=1e-12, atol=1e-14)
+    assert np.all(Z[~live] == 0.0)
+
+
+def test_round_counts_is_correct_rounding():
+    rng = np.random.default_rng(5)
+    C = rng.integers(0, 1 << 24, size=(400, 3), dtype=np.uint64)
+    nk = rng.integers(1, 1 << 24, size=3, dtype=np.int64)
+    # near-tie cases: quotients whose float32 rounding is hardest
+    C[0] = [1, 3, 16777215]
+    nk[:] = [3, 7, 16777213]
+    Z = oracle.round_counts(C, nk)
+    for u in range(C.shape[0]):
+        for k in range(3):
+            want = _pins.round_fraction_to_f32(Fraction(int(C[u, k]), int(nk[k])))
+            assert Z[u, k] == want, (u, k)
+
+
+def test_embed_rows_matches_dense():
+    n, s, K = 400, 3000, 4
+    edges, Y, w = _random_case(21, n, s, K, 0.1, True)
+    rows = np.array([0, 5, 17, 399, 200, 5])
+    r, Zr = oracle.embed_rows(edges, Y, K, rows, weights=w)
+    Zd = _pins.dense_embedding(edges, Y, K, weights=w)
+    assert np.array_equal(r, np.unique(rows))
+    np.testing.assert_allclose(Zr, Zd[r], rtol=1e-12, atol=1e-14)
+    edges_u, Yu, _ = _random_case(22, n, s, K, 0.1, False)
+    r, Zr, Cr = oracle.embed_rows(edges_u, Yu, K, rows, with_counts=True)
+    Zd = _pins.dense_embedding(edges_u, Yu, K)
+    nk = np.bincount(Yu[Yu >= 0], minlength=K)
+    np.testing.assert_allclose(Cr / np.maximum(nk, 1), Zd[r], rtol=1e-12, atol=1e-14)
+
+
+def test_embed_rows_laplacian_matches_dense():
+    scipy_csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    n, s, K = 120, 700, 3
+    edges = graphgen.random_graph(n, s, 31, self_loops=False)
+    Y = graphgen.labels(n, K, 32, 0.1)
+    w = graphgen.weights(s, 33)
+    rows = np.arange(0, n, 7)
+    r, Zr = oracle.embed_rows(edges, Y, K, rows, weights=w, laplacian=True)
+    A = _pins.dense_adjacency(edges, n, w)
+    S = np.eye(n) - scipy_csgraph.laplacian(A, normed=True)
+    S[A.sum(axis=1) == 0] = 0.0
+    expect = (S @ _pins.dense_projection(Y, K))[r]
+    np.testing.assert_allclose(Zr, expect, rtol=1e-12, atol=1e-14)
+
+
+def test_error_codes():
+    e = np.array([[0, 1]], np.int32)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.embed(e, np.array([0, 2], np.int32), 2)
+    assert ei.value.code == oracle.BAD_LABEL
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.embed(np.array([[0, 2]], np.int32), np.array([0, 1], np.int32), 2)
+    assert ei.value.code == oracle.BAD_NODE
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.embed(e, np.array([0, -2], np.int32), 2)
+    assert ei.value.code == oracle.BAD_LABEL
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.embed(e, np.array([0, 1], np.int32), 2,
+                     weights=np.array([-1.0], np.float32), laplacian=True)
+    assert ei.value.code == oracle.BAD_WEIGHT
+
+
+def _pins_all_hold() -> bool:
+    """Run a compact subset of the pins above; False if any fails."""
+    try:
+        for case in _pins.load_hand_cases():
+            test_hand_cases(case)
+        for seed in range(2):
+            test_dense_closed_form(seed, True)
+            test_dense_closed_form(seed, False)
+        test_single_class_is_degree_over_n()
+        for seed in range(2):
+            test_laplacian_matches_scipy_normalised_laplacian(seed, True)
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("mutation", range(1, 9))
+def test_pins_catch_planted_mistakes(mutation):
+    """Each planted oracle mistake (dropped update, wrong index, transposed
+    row, wrong class size, ...) must make at least one pin fail."""
+    assert _pins_all_hold()
+    oracle.set_mutation(mutation)
+    try:
+        assert not _pins_all_hold(), f"mutation {mutation} went unnoticed"
+    finally:
+        oracle.set_mutation(0)
+    assert _pins_all_hold()
