@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Throughput of the GEE edge-map pass (Z = A W) on GB300.
+
+A step is one full pass of the hot path over one label vector: label check
+and class histogram, then the edge pass with the 1/n_k scaling fused in,
+writing all of Z -- through the C ABI (gee_embed_graph) on a graph kept
+resident as a row-sorted CSR.  The default workload is the paper-scale
+synthetic graph: R-MAT (a, b, c) = (0.57, 0.19, 0.19) on 2^26 ids, n =
+65,600,000 nodes, s = 1,800,000,000 undirected unit-weight edges, K = 50,
+every node labelled.  Inputs (14.4 GB of arcs, 13.1 GB of Z) are far larger
+than L2, so no flush is needed between steps.
+
+Printed JSON line (rank 0): value = edges/s over all ranks; `roofline` for
+the dominant kernel (k_pull) from CUDA events recorded live on its stream;
+`e2e` the same metric through the host-buffer entry point with the label
+upload and the Z download inside the timed region; `cpu_baseline` the FP64
+oracle on a bounded sample; `oneshot` the edge-list entry point (gee_embed)
+that builds nothing resident.
+
+`--impl reference` times the oracle (serial C, FP64) on the host cores
+instead, on bounded samples of the same workload.
+
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
+data path; a gloo barrier brackets the timed region and the slowest rank's
+time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "paper": dict(desc="paper-scale R-MAT (Friendster-sized): n=65.6M, s=1.8B "
+                       "undirected unit-weight edges, K=50, all labelled",
+                  scale=26, n=65_600_000, s=1_800_000_000, K=50, frac_unlabeled=0.0,
+                  weighted=False, laplacian=False, seed=3),
+    "paper10": dict(desc="paper-scale R-MAT, 10% of nodes labelled",
+                    scale=26, n=65_600_000, s=1_800_000_000, K=50, frac_unlabeled=0.9,
+                    weighted=False, laplacian=False, seed=3),
+    "rmat24": dict(desc="R-MAT scale 24, edge factor 16, float weights in (0,1], K=20, "
+                        "10% unlabelled",
+                   scale=24, n=1 << 24, s=268_435_456, K=20, frac_unlabeled=0.1,
+                   weighted=True, laplacian=False, seed=2),
+    "rmat24lap": dict(desc="R-MAT scale 24 weighted, Laplacian variant",
+                      scale=24, n=1 << 24, s=268_435_456, K=20, frac_unlabeled=0.1,
+                      weighted=True, laplacian=True, seed=2),
+}
+METRIC = "GEE edges/s and % HBM roofline at 1.8B edges"
+PAPER_CONTEXT = ("paper: GEE-Ligra 6.42 s on Friendster (65M nodes, 1.8B edges), "
+                 "24-core Xeon 8259CL = 0.28e9 edges/s (different machine and graph)")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2402_04403_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != source_digest():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.out = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            ident = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if ident:
+            cmd += ["-i", ident]
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=self.out, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            text, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            text = ""
+        rows = []
+        for line in text.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(w):
+    """Compulsory bytes of one step: read the edges (8 B each, +4 B weight),
+    read Y once (4 B per node), write Z once (4 B per cell)."""
+    return w["s"] * (8 + 4 * w["weighted"]) + 4 * w["n"] + 4 * w["n"] * w["K"]
+
+
+def pull_bytes(w):
+    """Compulsory bytes of the edge-pass kernel: edges, the compact (1 B)
+    labels once, Z once."""
+    return w["s"] * (8 + 4 * w["weighted"]) + w["n"] + 4 * w["n"] * w["K"]
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def sample_inputs(w, shift, use_gpu):
+    """The workload shrunk by 2^shift (same generator, a, b, c, K, label mix)."""
+    import numpy as np
+    import graphgen
+    scale = w["scale"] - shift
+    n = max(1, w["n"] >> shift)
+    s = max(1, w["s"] >> shift)
+    if use_gpu:
+        e = graphgen.rmat_edges_device(scale, n, 0, s, w["seed"]).cpu().numpy()
+        Y = graphgen.labels_device(n, w["K"], w["seed"] + 1, w["frac_unlabeled"]).cpu().numpy()
+        wt = graphgen.weights_device(s, w["seed"] + 2).cpu().numpy() if w["weighted"] else None
+    else:
+        e = graphgen.rmat_edges(scale, n, 0, s, w["seed"])
+        Y = graphgen.labels(n, w["K"], w["seed"] + 1, w["frac_unlabeled"])
+        wt = graphgen.weights(s, w["seed"] + 2) if w["weighted"] else None
+    return dict(edges=np.ascontiguousarray(e), Y=Y, weights=wt, n=n, s=s, scale=scale)
+
+
+def time_oracle(sample, w):
+    import oracle
+    t = time.perf_counter()
+    oracle.embed(sample["edges"], sample["Y"], w["K"], weights=sample["weights"],
+                 laplacian=w["laplacian"])
+    return time.perf_counter() - t
+
+
+def cpu_baseline(w, use_gpu, shift=5):
+    smp = sample_inputs(w, shift, use_gpu)
+    secs = time_oracle(smp, w)
+    return {"value": smp["s"] / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": (f"R-MAT scale {smp['scale']}: n={smp['n']}, s={smp['s']} "
+                       f"(1/{1 << shift} of the workload, same generator and label mix), "
+                       f"serial C FP64 oracle, {secs:.2f} s"),
+            "seconds": secs}
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return
+    import torch
+    use_gpu = torch.cuda.is_available()
+    # size each step's sample so the whole run stays near two minutes
+    probe = sample_inputs(w, 12, use_gpu)
+    rate = probe["s"] / max(time_oracle(probe, w), 1e-4)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    shift = 12
+    while shift > 4 and (w["s"] >> (shift - 1)) / rate < per_step:
+        shift -= 1
+    smp = sample_inputs(w, shift, use_gpu)
+    for _ in range(args.warmup):
+        time_oracle(smp, w)
+    times = [time_oracle(smp, w) for _ in range(args.steps)]
+    total = sum(times)
+    value = smp["s"] * args.steps / total
+    sample = (f"R-MAT scale {smp['scale']}: n={smp['n']}, s={smp['s']} per step "
+              f"(1/{1 << shift} of the workload), serial C FP64 oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_for(args, w),
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_for(args, w):
+    return {"workload": w["desc"], "name": args.workload, "n": w["n"], "s": w["s"],
+            "K": w["K"], "weighted": w["weighted"], "laplacian": w["laplacian"],
+            "generator": "R-MAT a=0.57 b=0.19 c=0.19, Philox4x32-10 seed "
+                         f"{w['seed']}, ids permuted",
+            "graph": "resident row-sorted CSR (built once per graph, ingest timed apart)",
+            "l2": "inputs larger than L2, no flush", "parallelism": "replicas",
+            "context": PAPER_CONTEXT}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def run_ours(args, w, world, rank, local):
+    import torch
+
+    import graphgen
+    import paper_2402_04403_gb300 as gee
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, s, K = w["n"], w["s"], w["K"]
+
+    t0 = time.perf_counter()
+    edges = graphgen.rmat_edges_device(w["scale"], n, 0, s, w["seed"], device=dev)
+    Y = graphgen.labels_device(n, K, w["seed"] + 1, w["frac_unlabeled"], device=dev)
+    wts = graphgen.weights_device(s, w["seed"] + 2, device=dev) if w["weighted"] else None
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    g = gee.Graph(edges, n, weights=wts)
+    torch.cuda.synchronize()
+    ingest_s = time.perf_counter() - t0
+    info = g.info()
+    lap = w["laplacian"]
+    Z = torch.empty((n, K), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        g.embed(Y, K, laplacian=lap, out=Z)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    barrier(world)
+    torch.cuda.synchronize()
+    gee.profile_read()  # drop warm-up records
+    gee.profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.embed(Y, K, laplacian=lap, out=Z)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gee.profile_enable(False)
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    prof = gee.profile_read()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    ms_per_step = ms_max / args.steps
+    value = world * s / (ms_per_step / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    pull = prof.get("k_pull", {"launches": 0, "total_ms": float("nan")})
+    pull_ms = pull["total_ms"] / max(1, pull["launches"])
+    achieved = pull_bytes(w) / (pull_ms / 1e3) / 1e9
+    step_gbs = algorithmic_bytes(w) / (ms_per_step / 1e3) / 1e9
+    launches = sum(v["launches"] for v in prof.values())
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if (w["weighted"] or lap) else "u32", "data": "synthetic",
+        "config": config_for(args, w),
+        "roofline": {"bound": "hbm", "kernel": "k_pull", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "traffic": ncu_traffic("k_pull", args.workload),
+                     "algorithmic_bytes_per_launch": pull_bytes(w),
+                     "avg_launch_ms": pull_ms,
+                     "step_algorithmic_bytes": algorithmic_bytes(w),
+                     "step_gbs": step_gbs, "step_frac": step_gbs / peak,
+                     "frac_of_nominal_8tbs": step_gbs / 8000.0},
+        "kernels": {k: {"launches": v["launches"],
+                        "avg_ms": v["total_ms"] / max(1, v["launches"])}
+                    for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "ingest": {"graph_build_s": ingest_s, "generate_s": gen_s,
+                   "hub_rows": info["hub_rows"], "graph_device_bytes": info["device_bytes"]},
+    }
+
+    if not args.no_e2e:
+        Yh = Y.cpu().pin_memory()
+        Zh = torch.empty((n, K), dtype=torch.float32).pin_memory()
+        g.embed_host(Yh, K, laplacian=lap, out=Zh)
+        barrier(world)
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.embed_host(Yh, K, laplacian=lap, out=Zh)
+        e2e_s = max_over_ranks(time.perf_counter() - t, world) / args.e2e_steps
+        result["e2e"] = {"value": world * s / e2e_s, "unit": "edges/s",
+                         "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n * K,
+                         "ms_per_step": 1e3 * e2e_s,
+                         "api": "gee_embed_graph_host (pinned host Y and Z)"}
+        del Zh, Yh
+
+    if not args.no_oneshot:
+        g_close_first = args.workload.startswith("paper")
+        if g_close_first:
+            g.close()  # free the CSR so the one-shot scratch fits comfortably
+        gee.embed(edges, Y, K, weights=wts, laplacian=lap, out=Z)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.oneshot_steps):
+            gee.embed(edges, Y, K, weights=wts, laplacian=lap, out=Z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        os_ms = e0.elapsed_time(e1) / args.oneshot_steps
+        result["oneshot"] = {"value": s / (os_ms / 1e3), "unit": "edges/s",
+                             "ms_per_step": os_ms,
+                             "strategy": gee.pick_strategy(s, n, K),
+                             "api": "gee_embed (edge list in, Z out, nothing resident)"}
+    g.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, True, shift=args.cpu_shift)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--oneshot-steps", type=int, default=3)
+    ap.add_argument("--cpu-shift", type=int, default=5,
+                    help="cpu_baseline sample = workload / 2^shift")
+    ap.add_argument("--scale-shift", type=int, default=0,
+                    help="shrink the workload by 2^shift (same generator; for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oneshot", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    w = dict(WORKLOADS[args.workload])
+    if args.scale_shift:
+        sh = args.scale_shift
+        w.update(scale=w["scale"] - sh, n=w["n"] >> sh, s=w["s"] >> sh,
+                 desc=w["desc"] + f" (shrunk by 2^{sh}: n={w['n'] >> sh}, s={w['s'] >> sh})")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+    else:
+        run_ours(args, w, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -237,3 +237,89 @@ def random_graph(n, s, seed, self_loops=True):
     if not self_loops:
         v = np.where(u == v, (v + 1) % max(n, 1), v)
     return np.stack([u, v], axis=1).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# device generation (graphgen.cu): the same values, drawn on the GPU
+# ----------------------------------------------------------------------------
+import ctypes as _ctypes
+import os as _os
+import subprocess as _subprocess
+import threading as _threading
+
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+_CU = _os.path.join(_HERE, "graphgen.cu")
+_SO = _os.path.join(_HERE, "libgraphgen.so")
+_lock = _threading.Lock()
+_dev_lib = None
+
+
+def build(force=False):
+    """Compile graphgen.cu into libgraphgen.so (sm_103a) in place."""
+    if force or not _os.path.exists(_SO) or _os.path.getmtime(_SO) < _os.path.getmtime(_CU):
+        nvcc = _os.environ.get("NVCC") or "nvcc"
+        tmp = _SO + f".tmp{_os.getpid()}"
+        _subprocess.check_call([
+            nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
+            "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-shared",
+            "-cudart", "static", "-Xlinker", "--exclude-libs,ALL", "-o", tmp, _CU])
+        _os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _dev_lib
+    with _lock:
+        if _dev_lib is None:
+            lib = _ctypes.CDLL(build())
+            P, I64, I32, U32, U64 = (_ctypes.c_void_p, _ctypes.c_int64, _ctypes.c_int32,
+                                     _ctypes.c_uint32, _ctypes.c_uint64)
+            lib.graphgen_rmat.argtypes = [P, I64, I64, _ctypes.c_int, I64, U32, U32, U32, U64, P]
+            lib.graphgen_labels.argtypes = [P, I64, I64, I32, U64, U64, P]
+            lib.graphgen_weights.argtypes = [P, I64, I64, U64, P]
+            for f in (lib.graphgen_rmat, lib.graphgen_labels, lib.graphgen_weights):
+                f.restype = _ctypes.c_int
+            _dev_lib = lib
+    return _dev_lib
+
+
+def _stream():
+    import torch
+    return _ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def rmat_edges_device(scale, n, start, count, seed, a=0.57, b=0.19, c=0.19,
+                      out=None, device="cuda"):
+    """Same edges as rmat_edges, drawn on the GPU into an int32 (count, 2) tensor."""
+    import torch
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.int32, device=device)
+    A, AB, ABC = rmat_thresholds(a, b, c)
+    rc = _lib().graphgen_rmat(_ctypes.c_void_p(out.data_ptr()), start, count, scale, n,
+                              A, AB, ABC, int(seed) & 0xFFFFFFFFFFFFFFFF, _stream())
+    if rc != 0:
+        raise RuntimeError(f"graphgen_rmat failed ({rc})")
+    return out
+
+
+def labels_device(n, K, seed, frac_unlabeled=0.0, start=0, out=None, device="cuda"):
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=device)
+    rc = _lib().graphgen_labels(_ctypes.c_void_p(out.data_ptr()), start, n, K,
+                                unlabeled_threshold(frac_unlabeled),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, _stream())
+    if rc != 0:
+        raise RuntimeError(f"graphgen_labels failed ({rc})")
+    return out
+
+
+def weights_device(s, seed, start=0, out=None, device="cuda"):
+    import torch
+    if out is None:
+        out = torch.empty(s, dtype=torch.float32, device=device)
+    rc = _lib().graphgen_weights(_ctypes.c_void_p(out.data_ptr()), start, s,
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, _stream())
+    if rc != 0:
+        raise RuntimeError(f"graphgen_weights failed ({rc})")
+    return out

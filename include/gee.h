@@ -1,0 +1,196 @@
+/*
+ * gee.h -- C ABI of libgee: One-Hot Graph Encoder Embedding (GEE) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: "Edge-Parallel Graph Encoder Embedding" (Lubonja, Shen, Priebe,
+ * Burns; arXiv 2402.04403), Algorithm 1.  Given an edge list E (s edges
+ * (u, v, w)) and a label vector Y over n nodes with K classes, GEE builds the
+ * projection W(i, Y(i)) = 1 / count(Y = Y(i)) (Alg. 1, W initialisation) and
+ * in one pass over the edges accumulates
+ *     Z(u, Y(v)) += W(v, Y(v)) * w      and      Z(v, Y(u)) += W(u, Y(u)) * w
+ * (Alg. 1, loop body), i.e. Z = A W with A = M + M^T.
+ *
+ * Conventions shared by every entry point:
+ *   - edges: int32 [s][2] row-major, (u, v) per edge, 0 <= u, v < n.  Each
+ *     listed edge applies both updates (Section II: an undirected graph is
+ *     two symmetric directed graphs; list each undirected edge once).  A
+ *     self-loop adds 2w / n_k to Z[u, Y[u]].  Repeated edges add up.
+ *   - weights: float32 [s] or NULL for unit weights (Section II).
+ *   - Y: int32 [n]; 0..K-1 are classes, -1 means "class unknown" (the paper's
+ *     label 0).  Unknown nodes contribute nothing but still receive a Z row.
+ *     A class with no member gives an all-zero column.
+ *   - K: 1 <= K <= GEE_MAX_CLASSES.
+ *   - Z: float32 [n][K] row-major, written in full by every successful call.
+ *   - laplacian != 0 selects the Laplacian variant, which the paper leaves
+ *     out (Section II, end of the GEE paragraph).  Reading used: with
+ *     d_u = sum of the weights of u's edges (a self-loop counts twice), every
+ *     weight becomes w / sqrt(d_u d_v) before the pass.  Needs w >= 0.
+ *   - Precision: unit weights without the Laplacian accumulate exact uint32
+ *     counts C and give Z = RN32(C / n_k) (round to nearest float32 of the
+ *     exact quotient), identical bit for bit on every run.  Weighted and
+ *     Laplacian results accumulate in float32 and are scaled once per cell.
+ *   - Pointers named *_h are host memory; all others are device memory of
+ *     the current CUDA device.  The caller owns every buffer it passes.
+ *   - Every call is enqueued on `stream` and returns after the stream has
+ *     finished the call's work (it reads back a device status word), so the
+ *     result is ready when the call returns GEE_OK.
+ *   - Inputs are validated on the device before Z is touched: with
+ *     GEE_ERR_LABEL_RANGE, or GEE_ERR_NODE_RANGE under the default options,
+ *     Z is left unmodified.  Scratch memory comes from a stream-ordered pool
+ *     owned by the library (one per device, kept between calls).
+ *   - Calls on different streams may run concurrently.  A gee_graph may be
+ *     used from several streams at once.
+ */
+#ifndef GEE_H
+#define GEE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GEE_API __attribute__((visibility("default")))
+#else
+#define GEE_API
+#endif
+
+/* Same handle type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *gee_stream_t;
+
+#define GEE_MAX_CLASSES 255
+
+typedef enum gee_status {
+    GEE_OK = 0,
+    GEE_ERR_INVALID_ARG = 1,  /* bad scalar, NULL pointer, negative weight with
+                                 the Laplacian variant */
+    GEE_ERR_LABEL_RANGE = 2,  /* some Y[i] outside [-1, K) */
+    GEE_ERR_NODE_RANGE = 3,   /* some endpoint outside [0, n) */
+    GEE_ERR_OVERFLOW = 4,     /* a size does not fit the index types */
+    GEE_ERR_OOM = 5,          /* device memory exhausted */
+    GEE_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+    GEE_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
+    GEE_ERR_UNSUPPORTED = 8   /* e.g. K > GEE_MAX_CLASSES */
+} gee_status;
+
+/* Edge-pass strategy.  AUTO picks PRIVATE when n*K fits in shared memory and
+ * ATOMIC otherwise; SEGMENTED (CSR by row, each Z row written once, no global
+ * atomics) is what a gee_graph always uses. */
+typedef enum gee_strategy {
+    GEE_AUTO = 0,
+    GEE_ATOMIC = 1,    /* edge stream, red.global atomics into Z */
+    GEE_PRIVATE = 2,   /* per-CTA copy of Z in shared memory, then merged */
+    GEE_SEGMENTED = 3  /* build CSR by row, then one pull pass per row tile */
+} gee_strategy;
+
+typedef struct gee_options {
+    int32_t strategy;          /* gee_strategy */
+    int32_t validate_edges;    /* 1: check all endpoints before touching Z
+                                  (one extra read of the edge list in the
+                                  ATOMIC/PRIVATE paths); 0: the pass checks
+                                  endpoints itself and skips bad edges, Z is
+                                  then unspecified on GEE_ERR_NODE_RANGE */
+    int64_t private_max_cells; /* PRIVATE only when n*K <= this (0 = the
+                                  shared-memory limit) */
+    int32_t block;             /* threads per CTA of the ATOMIC/PRIVATE pass
+                                  (0 = 256; multiple of 32, <= 1024) */
+    int32_t reserved;
+} gee_options;
+
+/* Fills *opts with the defaults (AUTO, validate_edges = 1). */
+GEE_API void gee_options_default(gee_options *opts);
+
+/* Human-readable name of a status code (static string). */
+GEE_API const char *gee_status_string(gee_status status);
+
+/*
+ * Class sizes n_k = #{i : Y[i] = k} (Alg. 1, W initialisation; Alg. 2 runs it
+ * as a parallel loop over k).  counts: device uint32 [K], overwritten.
+ * GEE_ERR_LABEL_RANGE if a label is outside [-1, K); counts is then
+ * unspecified.
+ */
+GEE_API gee_status gee_histogram(const int32_t *Y, int64_t n, int32_t K,
+                         uint32_t *counts, gee_stream_t stream);
+
+/*
+ * Z = A W for an edge list (Alg. 1 / Alg. 2 of the paper): one call from
+ * edges and labels to the embedding.  opts may be NULL (defaults).
+ */
+GEE_API gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
+                     const int32_t *Y, int64_t n, int32_t K, int32_t laplacian,
+                     float *Z, const gee_options *opts, gee_stream_t stream);
+
+/* Same as gee_embed with host buffers: copies edges/weights/Y to the device,
+ * runs the pass and copies Z back to Z_h (pinned host memory is fastest). */
+GEE_API gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
+                          int64_t s, const int32_t *Y_h, int64_t n, int32_t K,
+                          int32_t laplacian, float *Z_h,
+                          const gee_options *opts, gee_stream_t stream);
+
+/*
+ * A graph kept resident on the device: the edge list is sorted by row into a
+ * symmetric CSR once (each edge (u,v,w) becomes arcs u->v and v->u; the
+ * arcs of rows with more than GEE_HUB_DEGREE arcs are kept apart and split
+ * into chunks).  This is the layout the paper's Ligra version iterates
+ * (Section III: edgeMapDense walks each node's edge list); repeated
+ * embeddings of the same graph with new label vectors then skip the upload
+ * and the sort.  Validates endpoints (GEE_ERR_NODE_RANGE, no graph).
+ * edges/weights are device pointers and are not referenced after return.
+ */
+#define GEE_HUB_DEGREE 4096
+typedef struct gee_graph gee_graph;
+
+GEE_API gee_status gee_graph_create(const int32_t *edges, const float *weights,
+                            int64_t s, int64_t n, gee_stream_t stream,
+                            gee_graph **out);
+
+/* Z = A W for a resident graph and a label vector Y (device int32 [n]). */
+GEE_API gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
+                           int32_t laplacian, float *Z,
+                           const gee_options *opts, gee_stream_t stream);
+
+/* Same with host Y_h and Z_h (e.g. pinned buffers). */
+GEE_API gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
+                                int32_t K, int32_t laplacian, float *Z_h,
+                                const gee_options *opts, gee_stream_t stream);
+
+/* Sizes of a resident graph; any output pointer may be NULL. */
+GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
+                          int64_t *hub_rows, int64_t *device_bytes);
+
+/* Frees the graph after all device work has finished.  NULL is a no-op. */
+GEE_API void gee_graph_destroy(gee_graph *graph);
+
+/* The strategy gee_embed would run for these sizes and options. */
+GEE_API gee_strategy gee_pick_strategy(int64_t s, int64_t n, int32_t K,
+                               const gee_options *opts);
+
+/* Upper bound of the scratch bytes gee_embed draws from the pool. */
+GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
+                           int32_t weighted, int32_t laplacian,
+                           const gee_options *opts);
+
+/*
+ * Tracing.  While enabled (process-wide), every kernel launch of the library
+ * is bracketed by two CUDA events on the stream it is launched on.
+ * gee_profile_read waits for the recorded events, fills up to max_entries
+ * per-kernel totals (sorted by name), clears the record and returns the
+ * number of distinct kernels seen.  Adds two event records per launch.
+ */
+typedef struct gee_kernel_time {
+    char name[32];      /* kernel name, NUL-terminated */
+    int64_t launches;   /* launches recorded */
+    double total_ms;    /* sum of event-to-event durations */
+    double max_ms;      /* longest launch */
+} gee_kernel_time;
+
+GEE_API void gee_profile_enable(int32_t on);
+GEE_API int32_t gee_profile_read(gee_kernel_time *out, int32_t max_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEE_H */

@@ -1,0 +1,245 @@
+"""GB300-native One-Hot Graph Encoder Embedding (GEE).
+
+Python binding of libgee.so (include/gee.h): the functions below check and
+marshal PyTorch tensors (device memory, streams) and call the C ABI; every
+step of the embedding -- label check and histogram, edge pass, scaling --
+runs in the library's CUDA kernels.  Method: Algorithm 1 of "Edge-Parallel
+Graph Encoder Embedding" (arXiv 2402.04403): Z = A W with
+W(i, Y(i)) = 1 / count(Y = Y(i)).
+
+Conventions: ``edges`` int32 (s, 2) of (u, v); ``weights`` float32 (s,) or
+None for unit weights; ``Y`` int32 (n,) with classes 0..K-1 and -1 for
+"class unknown"; result ``Z`` float32 (n, K).
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._lib import (GeeError, HUB_DEGREE, MAX_CLASSES, STATUS, STATUS_NAMES,
+                   STRATEGIES, STRATEGY_NAMES, KernelTime, check, lib, options)
+
+__all__ = ["GeeError", "Graph", "embed", "embed_host", "histogram",
+           "pick_strategy", "workspace_bytes", "status_string", "STATUS",
+           "STRATEGIES", "MAX_CLASSES", "HUB_DEGREE", "load", "profile_enable",
+           "profile_read"]
+
+
+def load():
+    """Load libgee.so now (raises if it is missing)."""
+    return lib()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, name, shape=None):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() > 0 else None
+
+
+def _edges_shape(edges):
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must have shape (s, 2)")
+    return edges.shape[0]
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start/stop CUDA-event tracing of every library kernel launch."""
+    lib().gee_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{kernel name: {"launches", "total_ms", "max_ms"}} since the last read."""
+    buf = (KernelTime * 64)()
+    got = lib().gee_profile_read(buf, len(buf))
+    out = {}
+    for i in range(min(got, len(buf))):
+        t = buf[i]
+        out[t.name.decode()] = {"launches": int(t.launches), "total_ms": float(t.total_ms),
+                                "max_ms": float(t.max_ms)}
+    return out
+
+
+def status_string(code: int) -> str:
+    return lib().gee_status_string(int(code)).decode()
+
+
+def histogram(Y, K: int, stream=None):
+    """Class sizes n_k (int32 tensor of length K; the library writes uint32)."""
+    torch = _torch()
+    n = Y.numel()
+    counts = torch.empty(K, dtype=torch.int32, device=Y.device)
+    rc = lib().gee_histogram(_dev_ptr(Y, torch.int32, "Y"), n, int(K),
+                             ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream))
+    check(rc, "gee_histogram")
+    return counts
+
+
+def pick_strategy(s: int, n: int, K: int, strategy="auto", private_max_cells=0) -> str:
+    o = options(strategy, True, private_max_cells)
+    return STRATEGY_NAMES[lib().gee_pick_strategy(int(s), int(n), int(K), ctypes.byref(o))]
+
+
+def workspace_bytes(s, n, K, weighted=False, laplacian=False, strategy="auto") -> int:
+    o = options(strategy)
+    return int(lib().gee_workspace_bytes(int(s), int(n), int(K), int(bool(weighted)),
+                                         int(bool(laplacian)), ctypes.byref(o)))
+
+
+def embed(edges, Y, K: int, weights=None, laplacian: bool = False, *,
+          strategy="auto", validate_edges: bool = True, block: int = 0,
+          private_max_cells: int = 0, out=None, stream=None):
+    """Z = A W for a device edge list (gee_embed)."""
+    torch = _torch()
+    s = _edges_shape(edges)
+    n = Y.numel()
+    if out is None:
+        out = torch.empty((n, K), dtype=torch.float32, device=Y.device)
+    o = options(strategy, validate_edges, private_max_cells, block)
+    rc = lib().gee_embed(
+        _dev_ptr(edges, torch.int32, "edges"),
+        _dev_ptr(weights, torch.float32, "weights", (s,)),
+        s, _dev_ptr(Y, torch.int32, "Y", (n,)), n, int(K), int(bool(laplacian)),
+        _dev_ptr(out, torch.float32, "out", (n, K)), ctypes.byref(o),
+        _stream_handle(stream))
+    check(rc, "gee_embed")
+    return out
+
+
+def _host_ptr(a, dtype, name, shape=None):
+    import numpy as np
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy {np.dtype(dtype)} array")
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}")
+    return ctypes.c_void_p(a.ctypes.data) if a.size else None
+
+
+def _host_buf(a):
+    """numpy array or pinned CPU tensor -> (pointer, numpy-like view)."""
+    try:
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or not a.is_contiguous():
+                raise TypeError("host buffers must be contiguous CPU tensors")
+            return a.numpy()
+    except ImportError:
+        pass
+    return a
+
+
+def embed_host(edges, Y, K: int, weights=None, laplacian: bool = False, *,
+               strategy="auto", validate_edges: bool = True, out=None, stream=None):
+    """gee_embed_host: host (numpy or pinned CPU tensor) inputs and output;
+    the library copies them to and from the device."""
+    import numpy as np
+    edges, Y, weights = _host_buf(edges), _host_buf(Y), _host_buf(weights)
+    s = edges.shape[0]
+    n = Y.size
+    if out is None:
+        out = np.empty((n, K), dtype=np.float32)
+    outv = _host_buf(out)
+    o = options(strategy, validate_edges)
+    rc = lib().gee_embed_host(
+        _host_ptr(edges, np.int32, "edges", (s, 2)),
+        _host_ptr(weights, np.float32, "weights", (s,)), s,
+        _host_ptr(Y, np.int32, "Y", (n,)), n, int(K), int(bool(laplacian)),
+        _host_ptr(outv, np.float32, "out", (n, K)), ctypes.byref(o),
+        _stream_handle(stream))
+    check(rc, "gee_embed_host")
+    return out
+
+
+class Graph:
+    """A graph kept resident on the device as a symmetric CSR
+    (gee_graph_create); embeds label vectors with gee_embed_graph."""
+
+    def __init__(self, edges, n: int, weights=None, stream=None):
+        torch = _torch()
+        s = _edges_shape(edges)
+        h = ctypes.c_void_p()
+        rc = lib().gee_graph_create(
+            _dev_ptr(edges, torch.int32, "edges"),
+            _dev_ptr(weights, torch.float32, "weights", (s,)), s, int(n),
+            _stream_handle(stream), ctypes.byref(h))
+        check(rc, "gee_graph_create")
+        self._h = h
+        self.n = int(n)
+        self.s = int(s)
+        self.device = edges.device
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("graph is closed")
+        return self._h
+
+    def info(self) -> dict:
+        vals = [ctypes.c_int64() for _ in range(4)]
+        check(lib().gee_graph_info(self.handle, *[ctypes.byref(v) for v in vals]),
+              "gee_graph_info")
+        return dict(zip(("n", "s", "hub_rows", "device_bytes"), (v.value for v in vals)))
+
+    def embed(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.n, K), dtype=torch.float32, device=Y.device)
+        o = options()
+        rc = lib().gee_embed_graph(
+            self.handle, _dev_ptr(Y, torch.int32, "Y", (self.n,)), int(K),
+            int(bool(laplacian)), _dev_ptr(out, torch.float32, "out", (self.n, K)),
+            ctypes.byref(o), _stream_handle(stream))
+        check(rc, "gee_embed_graph")
+        return out
+
+    def embed_host(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+        import numpy as np
+        Yv = _host_buf(Y)
+        if out is None:
+            out = np.empty((self.n, K), dtype=np.float32)
+        outv = _host_buf(out)
+        o = options()
+        rc = lib().gee_embed_graph_host(
+            self.handle, _host_ptr(Yv, np.int32, "Y", (self.n,)), int(K),
+            int(bool(laplacian)), _host_ptr(outv, np.float32, "out", (self.n, K)),
+            ctypes.byref(o), _stream_handle(stream))
+        check(rc, "gee_embed_graph_host")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gee_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,670 @@
+// gee_api.cu -- the C ABI of libgee (declared in include/gee.h): argument
+// checks, scratch memory, strategy choice, launch sequence and status
+// read-back.  Every kernel lives in gee_coo.cu or gee_csr.cu.
+#include <mutex>
+#include <vector>
+
+#include "gee_internal.cuh"
+
+namespace gee {
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int g_sms[kMaxDevices];
+cudaMemPool_t g_pool[kMaxDevices];
+bool g_pool_ready[kMaxDevices];
+
+gee_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return GEE_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return GEE_ERR_OOM;
+    return GEE_ERR_CUDA;
+}
+
+// The library's stream-ordered pool on the current device.  Freed blocks stay
+// cached in the pool (release threshold = max) so repeated calls do not go
+// back to the driver.
+cudaError_t device_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_pool_ready[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess)
+            return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold,
+                                    &keep);
+        if (e != cudaSuccess)
+            return e;
+        g_pool[dev] = pool;
+        g_pool_ready[dev] = true;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// Scratch of one call: stream-ordered allocations released (to the pool) on
+// the same stream when the call returns.
+class Workspace : public Allocator {
+  public:
+    explicit Workspace(cudaStream_t s) : stream_(s) {}
+    ~Workspace() override
+    {
+        for (void *p : ptrs_)
+            cudaFreeAsync(p, stream_);
+    }
+    cudaError_t alloc(void **p, size_t bytes) override
+    {
+        if (!pool_) {
+            cudaError_t e = device_pool(&pool_);
+            if (e != cudaSuccess)
+                return e;
+        }
+        if (bytes == 0)
+            bytes = 16;
+        // round up so vector accesses past the logical end stay inside
+        bytes = (bytes + 255) & ~size_t(255);
+        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool_, stream_);
+        if (e == cudaSuccess)
+            ptrs_.push_back(*p);
+        return e;
+    }
+
+  private:
+    cudaStream_t stream_;
+    cudaMemPool_t pool_ = nullptr;
+    std::vector<void *> ptrs_;
+};
+
+// Long-lived arrays of a resident graph.
+class GraphAllocator : public Allocator {
+  public:
+    explicit GraphAllocator(std::vector<void *> *owned) : owned_(owned) {}
+    cudaError_t alloc(void **p, size_t bytes) override
+    {
+        if (bytes == 0)
+            bytes = 16;
+        bytes = (bytes + 255) & ~size_t(255);
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess)
+            owned_->push_back(*p);
+        return e;
+    }
+
+  private:
+    std::vector<void *> *owned_;
+};
+
+// Waits for the stream and returns the first status a kernel reported.
+gee_status read_status(const DevStatus *st, cudaStream_t stream)
+{
+    DevStatus h;
+    cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost,
+                                    stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess)
+        return from_cuda(e);
+    return static_cast<gee_status>(h.code);
+}
+
+gee_options resolve_options(const gee_options *opts)
+{
+    gee_options o;
+    gee_options_default(&o);
+    if (opts != nullptr)
+        o = *opts;
+    return o;
+}
+
+gee_status check_common(int64_t s, int64_t n, int32_t K, int32_t threads)
+{
+    if (s < 0 || n < 0 || K < 1)
+        return GEE_ERR_INVALID_ARG;
+    if (K > kMaxClasses)
+        return GEE_ERR_UNSUPPORTED;
+    if (n > INT32_MAX || s > (INT64_MAX / 4))
+        return GEE_ERR_OVERFLOW;
+    if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024))
+        return GEE_ERR_INVALID_ARG;
+    return GEE_OK;
+}
+
+#define GEE_CHECK_CUDA(x)                                                      \
+    do {                                                                       \
+        cudaError_t e_ = (x);                                                  \
+        if (e_ != cudaSuccess)                                                 \
+            return from_cuda(e_);                                              \
+    } while (0)
+
+// Scratch of one call: status word, n_k, compact labels (n + 16 bytes).
+gee_status step_begin(Workspace &ws, int64_t n, int32_t K, DevStatus **st,
+                      uint32_t **counts, uint8_t **Yc, cudaStream_t stream)
+{
+    GEE_CHECK_CUDA(ws.alloc((void **)st, sizeof(DevStatus)));
+    GEE_CHECK_CUDA(ws.alloc((void **)counts, sizeof(uint32_t) * kMaxClasses));
+    GEE_CHECK_CUDA(ws.alloc((void **)Yc, (size_t)n + 16));
+    {
+        ProfScope p("k_status_init", stream);
+        GEE_CHECK_CUDA(launch_status_init(*st, stream));
+    }
+    GEE_CHECK_CUDA(cudaMemsetAsync(*counts, 0, sizeof(uint32_t) * K, stream));
+    return GEE_OK;
+}
+
+// S1 + S2: label check, class sizes, compact labels (in rank order when the
+// graph has degree ranks).
+gee_status labels_launch(const int32_t *Y, int64_t n, int32_t K,
+                         const int32_t *rank, uint8_t *Yc, uint32_t *counts,
+                         DevStatus *st, cudaStream_t stream)
+{
+    if (n > 0) {
+        ProfScope p("k_labels", stream);
+        GEE_CHECK_CUDA(launch_labels(Y, n, K, rank, Yc, counts, st, stream));
+    }
+    return GEE_OK;
+}
+
+gee_status labels_step(Workspace &ws, const int32_t *Y, int64_t n, int32_t K,
+                       const int32_t *rank, DevStatus **st, uint32_t **counts,
+                       uint8_t **Yc, cudaStream_t stream)
+{
+    gee_status rc = step_begin(ws, n, K, st, counts, Yc, stream);
+    if (rc != GEE_OK)
+        return rc;
+    return labels_launch(Y, n, K, rank, *Yc, *counts, *st, stream);
+}
+
+// S4 + S5 over a CSR (resident or built for this call).
+gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
+                     const uint8_t *Yc, const uint32_t *counts, float *Z,
+                     const DevStatus *st, cudaStream_t stream)
+{
+    const int64_t ntiles = pull_tiles(g, K);
+    int32_t *tile_row = nullptr;
+    void *hub_part = nullptr;
+    unsigned long long *work = nullptr;
+    GEE_CHECK_CUDA(ws.alloc((void **)&work, sizeof(unsigned long long)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&tile_row,
+                            sizeof(int32_t) * (ntiles + 1)));
+    GEE_CHECK_CUDA(ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * K + 1)));
+    {
+        ProfScope p("k_partition", stream);
+        GEE_CHECK_CUDA(launch_partition(g, K, tile_row, ntiles, stream));
+    }
+    if (ntiles + g.chunks > 0) {
+        ProfScope p("k_pull", stream);
+        GEE_CHECK_CUDA(launch_pull(g, K, g.weighted, laplacian, tile_row,
+                                   ntiles, Yc, counts, Z, hub_part, work, st,
+                                   stream));
+    }
+    if (g.hubs > 0) {
+        ProfScope p("k_hub_fixup", stream);
+        GEE_CHECK_CUDA(launch_hub_fixup(g, K, g.weighted, laplacian, counts, Z,
+                                        hub_part, st, stream));
+    }
+    return GEE_OK;
+}
+
+// Edge-list embedding on device buffers; the caller reads the status.
+gee_status embed_coo(Workspace &ws, const int32_t *E, const float *w,
+                     int64_t s, const int32_t *Y, int64_t n, int32_t K,
+                     int32_t laplacian, float *Z, const gee_options &o,
+                     cudaStream_t stream, DevStatus **st_out)
+{
+    DevStatus *st;
+    uint32_t *counts;
+    uint8_t *Yc;
+    gee_status rc = step_begin(ws, n, K, &st, &counts, &Yc, stream);
+    *st_out = st;
+    if (rc != GEE_OK)
+        return rc;
+    const gee_strategy strat = gee_pick_strategy(s, n, K, &o);
+    const int threads = o.block != 0 ? o.block : 256;
+    if (strat == GEE_SEGMENTED) {
+        Csr g;
+        GEE_CHECK_CUDA(build_csr(E, w, s, n, ws, ws, g, st, stream));
+        rc = labels_launch(Y, n, K, g.rank, Yc, counts, st, stream);
+        if (rc != GEE_OK)
+            return rc;
+        rc = read_status(st, stream);
+        if (rc != GEE_OK)
+            return rc;
+        if (laplacian) {
+            if (g.negative_weight)
+                return GEE_ERR_INVALID_ARG;
+            GEE_CHECK_CUDA(build_laplacian_values(g, ws, ws, stream));
+        }
+        return pull_step(ws, g, K, laplacian != 0, Yc, counts, Z, st, stream);
+    }
+    rc = labels_launch(Y, n, K, nullptr, Yc, counts, st, stream);
+    if (rc != GEE_OK)
+        return rc;
+    float *r = nullptr;
+    bool check = false;
+    if (laplacian) {
+        double *d;
+        GEE_CHECK_CUDA(ws.alloc((void **)&d, sizeof(double) * (n + 1)));
+        GEE_CHECK_CUDA(ws.alloc((void **)&r, sizeof(float) * (n + 1)));
+        GEE_CHECK_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (n + 1), stream));
+        if (s > 0) {
+            ProfScope p("k_degree", stream);
+            GEE_CHECK_CUDA(launch_degree(E, w, s, n, d, st, stream));
+        }
+        if (n > 0) {
+            ProfScope p("k_rsqrt", stream);
+            GEE_CHECK_CUDA(launch_rsqrt(d, n, r, st, stream));
+        }
+    } else if (o.validate_edges) {
+        if (s > 0) {
+            ProfScope p("k_validate_edges", stream);
+            GEE_CHECK_CUDA(launch_validate_edges(E, s, n, st, stream));
+        }
+    } else {
+        check = true;
+    }
+    if (n > 0) {
+        ProfScope p("k_zero", stream);
+        GEE_CHECK_CUDA(launch_zero(Z, n * K, st, stream));
+    }
+    if (s > 0) {
+        ProfScope p(strat == GEE_PRIVATE ? "k_scatter_private"
+                                         : "k_scatter_atomic",
+                    stream);
+        if (strat == GEE_PRIVATE)
+            GEE_CHECK_CUDA(launch_scatter_private(E, w, r, s, n, K, Yc, Z,
+                                                  check, threads, st, stream));
+        else
+            GEE_CHECK_CUDA(launch_scatter_atomic(E, w, r, s, n, K, Yc, Z,
+                                                 check, threads, st, stream));
+    }
+    if (n > 0) {
+        ProfScope p("k_finalize", stream);
+        if (w != nullptr || laplacian)
+            GEE_CHECK_CUDA(
+                launch_finalize_weighted(Z, r, n, K, counts, st, stream));
+        else
+            GEE_CHECK_CUDA(launch_finalize_count(Z, n, K, counts, st, stream));
+    }
+    return GEE_OK;
+}
+
+}  // namespace
+
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return 148;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_sms[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
+                                   dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 148;
+        g_sms[dev] = sms;
+    }
+    return g_sms[dev];
+}
+
+}  // namespace gee
+
+using namespace gee;
+
+struct gee_graph {
+    int device = 0;
+    Csr csr;
+    std::vector<void *> owned;
+    std::mutex mu;
+    bool lap_ready = false;
+    cudaEvent_t lap_done = nullptr;
+};
+
+namespace {
+
+gee_status ensure_laplacian(gee_graph *g, cudaStream_t stream)
+{
+    std::lock_guard<std::mutex> lock(g->mu);
+    if (g->csr.negative_weight)
+        return GEE_ERR_INVALID_ARG;
+    if (!g->lap_ready) {
+        Workspace ws(stream);
+        GraphAllocator keep(&g->owned);
+        GEE_CHECK_CUDA(build_laplacian_values(g->csr, keep, ws, stream));
+        GEE_CHECK_CUDA(cudaEventRecord(g->lap_done, stream));
+        g->lap_ready = true;
+    }
+    GEE_CHECK_CUDA(cudaStreamWaitEvent(stream, g->lap_done, 0));
+    return GEE_OK;
+}
+
+gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
+                           int32_t K, int32_t laplacian, float *Z,
+                           cudaStream_t stream)
+{
+    if (laplacian) {
+        gee_status rc = ensure_laplacian(graph, stream);
+        if (rc != GEE_OK)
+            return rc;
+    }
+    DevStatus *st;
+    uint32_t *counts;
+    uint8_t *Yc;
+    gee_status rc =
+        labels_step(ws, Y, graph->csr.n, K, graph->csr.rank, &st, &counts, &Yc,
+                    stream);
+    if (rc != GEE_OK)
+        return rc;
+    rc = pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
+                   stream);
+    if (rc != GEE_OK)
+        return rc;
+    return read_status(st, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gee_options_default(gee_options *opts)
+{
+    if (opts == nullptr)
+        return;
+    opts->strategy = GEE_AUTO;
+    opts->validate_edges = 1;
+    opts->private_max_cells = 0;
+    opts->block = 0;
+    opts->reserved = 0;
+}
+
+const char *gee_status_string(gee_status status)
+{
+    switch (status) {
+    case GEE_OK: return "ok";
+    case GEE_ERR_INVALID_ARG: return "invalid argument";
+    case GEE_ERR_LABEL_RANGE: return "label outside [-1, K)";
+    case GEE_ERR_NODE_RANGE: return "edge endpoint outside [0, n)";
+    case GEE_ERR_OVERFLOW: return "size overflows the index types";
+    case GEE_ERR_OOM: return "out of device memory";
+    case GEE_ERR_CUDA: return "CUDA runtime error";
+    case GEE_ERR_TIMEOUT: return "device wait timed out";
+    case GEE_ERR_UNSUPPORTED: return "unsupported argument";
+    }
+    return "unknown status";
+}
+
+gee_strategy gee_pick_strategy(int64_t s, int64_t n, int32_t K,
+                               const gee_options *opts)
+{
+    const gee_options o = resolve_options(opts);
+    const int64_t limit = private_cells_limit();
+    const int64_t cells = n * (int64_t)K;
+    if (o.strategy == GEE_PRIVATE && cells > limit)
+        return GEE_ATOMIC;  // the copy would not fit in shared memory
+    if (o.strategy != GEE_AUTO)
+        return static_cast<gee_strategy>(o.strategy);
+    const int64_t cap =
+        o.private_max_cells > 0 && o.private_max_cells < limit
+            ? o.private_max_cells
+            : limit;
+    // PRIVATE pays once every SM's CTA has several edges per cell to merge.
+    if (cells <= cap && 2 * s >= 4 * cells * (int64_t)sm_count())
+        return GEE_PRIVATE;
+    return GEE_ATOMIC;
+}
+
+size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K, int32_t weighted,
+                           int32_t laplacian, const gee_options *opts)
+{
+    size_t b = 4096 + (size_t)n + 16 + 256 * 4;
+    const gee_strategy st = gee_pick_strategy(s, n, K, opts);
+    if (laplacian)
+        b += (size_t)(n + 1) * 12;
+    if (st == GEE_SEGMENTED) {
+        b += (size_t)(n + 1) * (8 * 4 + 4 * 4);  // rowptr, scan and fill temps
+        b += (size_t)(2 * s + 8) * 4 * (weighted || laplacian ? 3 : 1);
+        b += (size_t)((2 * s + n * K) / kTileUnits + 2) * 4;
+        b += (size_t)((2 * s) / kHubDegree + 2) * ((size_t)K * 4 + 12);
+    }
+    return b;
+}
+
+gee_status gee_histogram(const int32_t *Y, int64_t n, int32_t K,
+                         uint32_t *counts, gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    gee_status rc = check_common(0, n, K, 0);
+    if (rc != GEE_OK)
+        return rc;
+    if (counts == nullptr || (n > 0 && Y == nullptr))
+        return GEE_ERR_INVALID_ARG;
+    gee_status out;
+    {
+        Workspace ws(stream);
+        DevStatus *st;
+        uint32_t *c;
+        uint8_t *Yc;
+        rc = labels_step(ws, Y, n, K, nullptr, &st, &c, &Yc, stream);
+        if (rc != GEE_OK)
+            return rc;
+        cudaError_t e = cudaMemcpyAsync(counts, c, sizeof(uint32_t) * K,
+                                        cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess)
+            return from_cuda(e);
+        out = read_status(st, stream);
+    }
+    return out;
+}
+
+gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
+                     const int32_t *Y, int64_t n, int32_t K, int32_t laplacian,
+                     float *Z, const gee_options *opts, gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const gee_options o = resolve_options(opts);
+    gee_status rc = check_common(s, n, K, o.block);
+    if (rc != GEE_OK)
+        return rc;
+    if ((s > 0 && edges == nullptr) || (n > 0 && (Y == nullptr || Z == nullptr)))
+        return GEE_ERR_INVALID_ARG;
+    if (s > 0 && n == 0)
+        return GEE_ERR_NODE_RANGE;
+    if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
+        return GEE_ERR_INVALID_ARG;
+    Workspace ws(stream);
+    DevStatus *st = nullptr;
+    rc = embed_coo(ws, edges, weights, s, Y, n, K, laplacian, Z, o, stream,
+                   &st);
+    if (rc != GEE_OK)
+        return rc;
+    return read_status(st, stream);
+}
+
+gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
+                          int64_t s, const int32_t *Y_h, int64_t n, int32_t K,
+                          int32_t laplacian, float *Z_h,
+                          const gee_options *opts, gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const gee_options o = resolve_options(opts);
+    gee_status rc = check_common(s, n, K, o.block);
+    if (rc != GEE_OK)
+        return rc;
+    if ((s > 0 && edges_h == nullptr) ||
+        (n > 0 && (Y_h == nullptr || Z_h == nullptr)))
+        return GEE_ERR_INVALID_ARG;
+    if (s > 0 && n == 0)
+        return GEE_ERR_NODE_RANGE;
+    Workspace ws(stream);
+    int32_t *E = nullptr, *Y = nullptr;
+    float *w = nullptr, *Z = nullptr;
+    GEE_CHECK_CUDA(ws.alloc((void **)&E, sizeof(int32_t) * 2 * (s + 1)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&Y, sizeof(int32_t) * (n + 1)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
+    GEE_CHECK_CUDA(cudaMemcpyAsync(E, edges_h, sizeof(int32_t) * 2 * s,
+                                   cudaMemcpyHostToDevice, stream));
+    GEE_CHECK_CUDA(cudaMemcpyAsync(Y, Y_h, sizeof(int32_t) * n,
+                                   cudaMemcpyHostToDevice, stream));
+    if (weights_h != nullptr) {
+        GEE_CHECK_CUDA(ws.alloc((void **)&w, sizeof(float) * (s + 1)));
+        GEE_CHECK_CUDA(cudaMemcpyAsync(w, weights_h, sizeof(float) * s,
+                                       cudaMemcpyHostToDevice, stream));
+    }
+    DevStatus *st = nullptr;
+    rc = embed_coo(ws, E, w, s, Y, n, K, laplacian, Z, o, stream, &st);
+    if (rc != GEE_OK)
+        return rc;
+    rc = read_status(st, stream);
+    if (rc != GEE_OK)
+        return rc;
+    GEE_CHECK_CUDA(cudaMemcpyAsync(Z_h, Z, sizeof(float) * n * K,
+                                   cudaMemcpyDeviceToHost, stream));
+    GEE_CHECK_CUDA(cudaStreamSynchronize(stream));
+    return GEE_OK;
+}
+
+void gee_graph_destroy(gee_graph *graph)
+{
+    if (graph == nullptr)
+        return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(graph->device);
+    cudaDeviceSynchronize();
+    for (void *p : graph->owned)
+        cudaFree(p);
+    if (graph->lap_done)
+        cudaEventDestroy(graph->lap_done);
+    cudaSetDevice(prev);
+    delete graph;
+}
+
+gee_status gee_graph_create(const int32_t *edges, const float *weights,
+                            int64_t s, int64_t n, gee_stream_t stream_,
+                            gee_graph **out)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (out == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    *out = nullptr;
+    gee_status rc = check_common(s, n, 1, 0);
+    if (rc != GEE_OK)
+        return rc;
+    if (s > 0 && edges == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    if (s > 0 && n == 0)
+        return GEE_ERR_NODE_RANGE;
+    gee_graph *g = new gee_graph();
+    cudaGetDevice(&g->device);
+    gee_status result;
+    {
+        Workspace ws(stream);
+        GraphAllocator keep(&g->owned);
+        DevStatus *st = nullptr;
+        cudaError_t e = ws.alloc((void **)&st, sizeof(DevStatus));
+        if (e == cudaSuccess)
+            e = launch_status_init(st, stream);
+        if (e == cudaSuccess)
+            e = build_csr(edges, weights, s, n, keep, ws, g->csr, st, stream);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&g->lap_done,
+                                         cudaEventDisableTiming);
+        result = (e == cudaSuccess) ? read_status(st, stream) : from_cuda(e);
+    }
+    if (result != GEE_OK) {
+        gee_graph_destroy(g);
+        return result;
+    }
+    *out = g;
+    return GEE_OK;
+}
+
+gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
+                          int64_t *hub_rows, int64_t *device_bytes)
+{
+    if (graph == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    const Csr &c = graph->csr;
+    if (n)
+        *n = c.n;
+    if (s)
+        *s = c.s;
+    if (hub_rows)
+        *hub_rows = c.hubs;
+    if (device_bytes) {
+        int64_t b = (c.n + 1) * 8 + (c.nnz_main + 4) * 4 + (c.hub_arcs + 4) * 4;
+        if (c.weighted)
+            b += (c.nnz_main + c.hub_arcs + 8) * 4;
+        if (c.lap_val)
+            b += (c.nnz_main + c.hub_arcs + 8) * 4;
+        b += c.hubs * 16 + c.chunks * 12;
+        *device_bytes = b;
+    }
+    return GEE_OK;
+}
+
+gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
+                           int32_t laplacian, float *Z,
+                           const gee_options *opts, gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (graph == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    const gee_options o = resolve_options(opts);
+    gee_status rc = check_common(0, graph->csr.n, K, o.block);
+    if (rc != GEE_OK)
+        return rc;
+    if (graph->csr.n > 0 && (Y == nullptr || Z == nullptr))
+        return GEE_ERR_INVALID_ARG;
+    Workspace ws(stream);
+    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
+}
+
+gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
+                                int32_t K, int32_t laplacian, float *Z_h,
+                                const gee_options *opts, gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (graph == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    const gee_options o = resolve_options(opts);
+    const int64_t n = graph->csr.n;
+    gee_status rc = check_common(0, n, K, o.block);
+    if (rc != GEE_OK)
+        return rc;
+    if (n > 0 && (Y_h == nullptr || Z_h == nullptr))
+        return GEE_ERR_INVALID_ARG;
+    Workspace ws(stream);
+    int32_t *Y = nullptr;
+    float *Z = nullptr;
+    GEE_CHECK_CUDA(ws.alloc((void **)&Y, sizeof(int32_t) * (n + 1)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
+    GEE_CHECK_CUDA(cudaMemcpyAsync(Y, Y_h, sizeof(int32_t) * n,
+                                   cudaMemcpyHostToDevice, stream));
+    rc = embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
+    if (rc != GEE_OK)
+        return rc;
+    GEE_CHECK_CUDA(cudaMemcpyAsync(Z_h, Z, sizeof(float) * n * K,
+                                   cudaMemcpyDeviceToHost, stream));
+    GEE_CHECK_CUDA(cudaStreamSynchronize(stream));
+    return GEE_OK;
+}
+
+}  // extern "C"

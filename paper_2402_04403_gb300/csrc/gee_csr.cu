@@ -1,0 +1,1123 @@
+// gee_csr.cu -- the row-sorted (CSR) form of GEE's edge pass on sm_103a.
+//
+// The paper's Ligra version runs Alg. 1's loop body inside edgeMapDense, one
+// worker walking each node's edge list (Section III).  Here the same walk is
+// organised for a GPU:
+//
+//   build_csr      edge list -> symmetric CSR (each edge (u,v,w) gives arcs
+//                  u->v and v->u), rows with more than kHubDegree arcs moved
+//                  to a separate hub CSR cut into chunks of kHubDegree arcs.
+//   k_partition    splits rows + arcs into tiles of kTileUnits merged units
+//                  (1 per arc, K per row) so every tile moves ~16 KB.
+//   k_pull         per row tile: (A) coalesced arc load + label gather into
+//                  shared memory, (B) each thread walks its share of the
+//                  merged row/arc sequence and adds into a shared-memory
+//                  accumulator of the tile's rows, (C) the tile's Z rows --
+//                  contiguous in Z -- are scaled by 1/n_k and written once.
+//                  Hub chunks accumulate per-class partial sums.
+//   k_hub_fixup    sums each hub's chunk partials in a fixed order and
+//                  writes its Z row.
+//
+// No global atomics touch Z: every Z row is written exactly once (hub rows
+// twice: zeros by their row tile, then the fixup).
+#include "gee_internal.cuh"
+
+namespace gee {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int64_t kHubBit = int64_t(1) << 62;
+
+// ------------------------------------------------------------ block scan
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v,
+                                                        int64_t *warp_sums,
+                                                        int64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        warp_sums[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int64_t t = warp_sums[w];
+            warp_sums[w] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    const int64_t r = warp_sums[warp] + x - v;
+    __syncthreads();
+    return r;
+}
+
+template <class In>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_reduce(const In *__restrict__ in, int64_t n,
+                  int64_t *__restrict__ partial)
+{
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    __shared__ int64_t total;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t sum = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+        if (base + i < n)
+            sum += (int64_t)in[base + i];
+    block_exclusive_scan(sum, warp_sums, &total);
+    if (threadIdx.x == 0)
+        partial[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of the per-tile sums in place; total -> *out_total.
+__global__ void __launch_bounds__(1024)
+    k_scan_partials(int64_t *__restrict__ partial, int64_t nb,
+                    int64_t *__restrict__ out_total)
+{
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t total;
+    const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = threadIdx.x * per;
+    int64_t sum = 0;
+    for (int64_t i = b0; i < b0 + per && i < nb; ++i)
+        sum += partial[i];
+    int64_t run = block_exclusive_scan(sum, warp_sums, &total);
+    for (int64_t i = b0; i < b0 + per && i < nb; ++i) {
+        const int64_t t = partial[i];
+        partial[i] = run;
+        run += t;
+    }
+    if (threadIdx.x == 0)
+        *out_total = total;
+}
+
+template <class In, class Out>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_apply(const In *__restrict__ in, int64_t n,
+                 const int64_t *__restrict__ partial, Out *__restrict__ out)
+{
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    __shared__ int64_t total;
+    const int64_t base =
+        (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < n) ? (int64_t)in[base + j] : 0;
+        sum += v[j];
+    }
+    int64_t run =
+        block_exclusive_scan(sum, warp_sums, &total) + partial[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n)
+            out[base + j] = (Out)run;
+        run += v[j];
+    }
+}
+
+// out[0..n) = exclusive prefix sums of in, out[n] = total.
+template <class In, class Out>
+cudaError_t exclusive_scan(const In *in, int64_t n, Out *out, Allocator &tmp,
+                           cudaStream_t stream)
+{
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) {
+        return cudaMemsetAsync(out, 0, sizeof(Out), stream);
+    }
+    int64_t *partial = nullptr, *total = nullptr;
+    cudaError_t e = tmp.alloc((void **)&partial, sizeof(int64_t) * (nb + 1));
+    if (e != cudaSuccess)
+        return e;
+    total = partial + nb;
+    k_scan_reduce<In><<<(unsigned)nb, kScanThreads, 0, stream>>>(in, n,
+                                                                partial);
+    k_scan_partials<<<1, 1024, 0, stream>>>(partial, nb, total);
+    k_scan_apply<In, Out>
+        <<<(unsigned)nb, kScanThreads, 0, stream>>>(in, n, partial, out);
+    // out[n] = total (narrowing copy for 32-bit outputs)
+    if (sizeof(Out) == sizeof(int64_t))
+        e = cudaMemcpyAsync(out + n, total, sizeof(int64_t),
+                            cudaMemcpyDeviceToDevice, stream);
+    else
+        e = cudaMemcpyAsync(out + n, total, sizeof(Out),
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess)
+        return e;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ CSR build
+__device__ __forceinline__ bool node_ok(int32_t x, int64_t n)
+{
+    return (int64_t)(uint32_t)x < n;
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_edge(const int32_t *__restrict__ E,
+                                              int64_t s, F &&f)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < s; i += nthreads) {
+        const int2 e = __ldcs(reinterpret_cast<const int2 *>(E) + i);
+        f(e.x, e.y, i);
+    }
+}
+
+__global__ void k_csr_degree(const int32_t *__restrict__ E,
+                             const float *__restrict__ w, int64_t s,
+                             int64_t n, uint32_t *__restrict__ deg,
+                             DevStatus *st)
+{
+    for_each_edge(E, s, [&](int32_t u, int32_t v, int64_t i) {
+        if (!node_ok(u, n) || !node_ok(v, n)) {
+            report(st, GEE_ERR_NODE_RANGE, (unsigned long long)i);
+            return;
+        }
+        if (w != nullptr && !(w[i] >= 0.0f))
+            atomicMax(&st->aux, 1);  // negative weight: no Laplacian
+        atomicAdd(deg + u, 1u);
+        atomicAdd(deg + v, 1u);
+    });
+}
+
+// deg_main = deg for ordinary rows, 0 for hub rows; hub = 1 for hub rows.
+__global__ void k_classify(const uint32_t *__restrict__ deg, int64_t n,
+                           uint32_t *__restrict__ deg_main,
+                           uint32_t *__restrict__ hub)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const uint32_t d = deg[i];
+        const bool h = d > (uint32_t)kHubDegree;
+        deg_main[i] = h ? 0u : d;
+        hub[i] = h ? 1u : 0u;
+    }
+}
+
+__global__ void k_hub_list(const uint32_t *__restrict__ deg,
+                           const uint32_t *__restrict__ hub,
+                           const int64_t *__restrict__ hub_index, int64_t n,
+                           int32_t *__restrict__ hub_row,
+                           uint32_t *__restrict__ hub_deg,
+                           uint32_t *__restrict__ hub_nchunks)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        if (!hub[i])
+            continue;
+        const int64_t h = hub_index[i];
+        hub_row[h] = (int32_t)i;
+        hub_deg[h] = deg[i];
+        hub_nchunks[h] = (deg[i] + kHubChunk - 1) / kHubChunk;
+    }
+}
+
+__global__ void k_chunk_list(const int64_t *__restrict__ hub_ptr,
+                             const int32_t *__restrict__ hub_chunk0,
+                             int64_t hubs, int32_t *__restrict__ chunk_hub,
+                             int64_t *__restrict__ chunk_begin)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t h = tid; h < hubs; h += nthreads) {
+        const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
+        for (int32_t c = c0; c < c1; ++c) {
+            chunk_hub[c] = (int32_t)h;
+            chunk_begin[c] = hub_ptr[h] + (int64_t)(c - c0) * kHubChunk;
+        }
+    }
+}
+
+// base[i] = first arc slot of row i in the main CSR, or (hub slot | kHubBit).
+__global__ void k_base(const int64_t *__restrict__ rowptr,
+                       const uint32_t *__restrict__ hub,
+                       const int64_t *__restrict__ hub_index,
+                       const int64_t *__restrict__ hub_ptr, int64_t n,
+                       int64_t *__restrict__ base)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads)
+        base[i] = hub[i] ? (hub_ptr[hub_index[i]] | kHubBit) : rowptr[i];
+}
+
+
+// ------------------------------------------------------------ degree ranks
+// Nodes are ranked by decreasing degree (in buckets of a quarter octave) and
+// arcs store the rank of their target instead of its id.  The labels of the
+// highest-degree nodes -- the targets of most arcs in a power-law graph --
+// then sit at the front of the rank-ordered label array, where the pull
+// kernel keeps them in shared memory.
+constexpr int kRankBuckets = 129;
+
+__device__ __forceinline__ int rank_bucket(uint32_t d)
+{
+    if (d == 0u)
+        return kRankBuckets - 1;
+    const int oct = 31 - __clz(d);
+    int frac = 0;
+    if (oct >= 2)
+        frac = (int)((d >> (oct - 2)) & 3u);
+    else if (oct == 1)
+        frac = (int)((d & 1u) << 1);
+    return 127 - (4 * oct + frac);
+}
+
+__global__ void k_rank_hist(const uint32_t *__restrict__ deg, int64_t n,
+                            uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t h[kRankBuckets];
+    for (int b = threadIdx.x; b < kRankBuckets; b += blockDim.x)
+        h[b] = 0;
+    __syncthreads();
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads)
+        atomicAdd(&h[rank_bucket(deg[i])], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kRankBuckets; b += blockDim.x)
+        if (h[b])
+            atomicAdd(&counts[b], h[b]);
+}
+
+__global__ void k_rank_base(const uint32_t *__restrict__ counts,
+                            int64_t *__restrict__ base)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int b = 0; b < kRankBuckets; ++b) {
+            base[b] = run;
+            run += counts[b];
+        }
+    }
+}
+
+// rank[i] = base[bucket] + position inside the bucket (one atomic per warp
+// and bucket).  Ranks form a permutation of [0, n).
+__global__ void k_rank_assign(const uint32_t *__restrict__ deg, int64_t n,
+                              const int64_t *__restrict__ base,
+                              unsigned long long *__restrict__ cursor,
+                              int32_t *__restrict__ rank)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const int b = rank_bucket(deg[i]);
+        const unsigned active = __activemask();
+        const unsigned peers = __match_any_sync(active, b);
+        const int leader = __ffs(peers) - 1;
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned long long first = 0;
+        if (lane == leader)
+            first = atomicAdd(&cursor[b], (unsigned long long)__popc(peers));
+        first = __shfl_sync(peers, first, leader);
+        rank[i] = (int32_t)(base[b] + (int64_t)first + __popc(peers & lt));
+    }
+}
+
+// Arcs u->v and v->u of every edge; the arc stores the target's rank.
+__global__ void k_csr_fill(const int32_t *__restrict__ E,
+                           const float *__restrict__ w, int64_t s,
+                           const int64_t *__restrict__ base,
+                           const int32_t *__restrict__ rank,
+                           uint32_t *__restrict__ cursor,
+                           int32_t *__restrict__ col,
+                           float *__restrict__ val,
+                           int32_t *__restrict__ col_h,
+                           float *__restrict__ val_h, const DevStatus *st)
+{
+    if (failed(st))
+        return;
+    auto arc = [&](int32_t from, int32_t to, float wt) {
+        const int64_t b = base[from];
+        const int64_t slot = atomicAdd(cursor + from, 1u);
+        const int32_t target = rank[to];
+        if (b & kHubBit) {
+            const int64_t p = (b & ~kHubBit) + slot;
+            col_h[p] = target;
+            if (val_h)
+                val_h[p] = wt;
+        } else {
+            col[b + slot] = target;
+            if (val)
+                val[b + slot] = wt;
+        }
+    };
+    for_each_edge(E, s, [&](int32_t u, int32_t v, int64_t i) {
+        const float wt = (w != nullptr) ? w[i] : 1.0f;
+        arc(u, v, wt);
+        arc(v, u, wt);
+    });
+}
+
+// ------------------------------------------------------------ Laplacian
+// d_u (FP64 sum of the row's arc weights, or the arc count), r = 1/sqrt(d).
+__global__ void k_row_rsqrt(const int64_t *__restrict__ rowptr,
+                            const float *__restrict__ val, int64_t n,
+                            float *__restrict__ r)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const int64_t a0 = rowptr[i], a1 = rowptr[i + 1];
+        double d = 0.0;
+        if (val != nullptr)
+            for (int64_t a = a0; a < a1; ++a)
+                d += (double)val[a];
+        else
+            d = (double)(a1 - a0);
+        r[i] = d > 0.0 ? __frsqrt_rn((float)d) : 0.0f;
+    }
+}
+
+// Hub rows: one warp per hub, FP64 lane sums combined in a fixed tree.
+__global__ void k_hub_rsqrt(const int32_t *__restrict__ hub_row,
+                            const int64_t *__restrict__ hub_ptr,
+                            const float *__restrict__ val_h, int64_t hubs,
+                            float *__restrict__ r)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < hubs; h += nwarps) {
+        const int64_t a0 = hub_ptr[h], a1 = hub_ptr[h + 1];
+        double d = 0.0;
+        if (val_h != nullptr)
+            for (int64_t a = a0 + lane; a < a1; a += 32)
+                d += (double)val_h[a];
+        else
+            d = (lane == 0) ? (double)(a1 - a0) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0)
+            r[hub_row[h]] = d > 0.0 ? __frsqrt_rn((float)d) : 0.0f;
+    }
+}
+
+__global__ void k_scatter_by_rank(const float *__restrict__ r, int64_t n,
+                                  const int32_t *__restrict__ rank,
+                                  float *__restrict__ r_rank)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads)
+        r_rank[rank[i]] = r[i];
+}
+
+// Laplacian arc value w * r(row) * r(target); targets are ranks.
+__global__ void k_lap_values(const int64_t *__restrict__ rowptr,
+                             const int32_t *__restrict__ col,
+                             const float *__restrict__ val, int64_t n,
+                             const float *__restrict__ r,
+                             const float *__restrict__ r_rank,
+                             float *__restrict__ out)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const float ri = r[i];
+        for (int64_t a = rowptr[i]; a < rowptr[i + 1]; ++a) {
+            const float w = val ? val[a] : 1.0f;
+            out[a] = w * ri * r_rank[col[a]];
+        }
+    }
+}
+
+__global__ void k_lap_values_hub(const int32_t *__restrict__ hub_row,
+                                 const int64_t *__restrict__ hub_ptr,
+                                 const int32_t *__restrict__ col_h,
+                                 const float *__restrict__ val_h, int64_t hubs,
+                                 const float *__restrict__ r,
+                                 const float *__restrict__ r_rank,
+                                 float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < hubs; h += nwarps) {
+        const float ri = r[hub_row[h]];
+        for (int64_t a = hub_ptr[h] + lane; a < hub_ptr[h + 1]; a += 32) {
+            const float w = val_h ? val_h[a] : 1.0f;
+            out[a] = w * ri * r_rank[col_h[a]];
+        }
+    }
+}
+
+// ------------------------------------------------------------ partition
+// Units: 1 per arc, C = max(K, 16) per row (its Z write; the floor keeps the
+// rows of one tile, and so the shared-memory row table, bounded for small K).
+// tile_row[t] = first row whose end unit E_r = rowptr[r+1] + r*C lies at or
+// after t*kTileUnits (n if none).  Tile t owns rows [tile_row[t],
+// tile_row[t+1]) with all their arcs: at most ceil(kTileUnits / C) rows and
+// kTileUnits + kHubDegree arcs.
+__device__ __host__ inline int row_cost(int32_t K) { return K > 16 ? K : 16; }
+
+__global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
+                            int32_t K, int64_t ntiles,
+                            int32_t *__restrict__ tile_row)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t > ntiles)
+        return;
+    if (t == ntiles) {
+        tile_row[t] = (int32_t)n;
+        return;
+    }
+    const int64_t C = row_cost(K);
+    const int64_t diag = t * kTileUnits;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rowptr[mid + 1] + mid * C >= diag)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    tile_row[t] = (int32_t)lo;
+}
+
+// ------------------------------------------------------------ pull
+// Persistent: one CTA per SM, NG independent groups of 256 threads, each
+// synchronised by its own named barrier.  A group repeatedly takes the next
+// work item (row tile or hub chunk) from a global counter.  The CTA first
+// copies the labels of ranks [0, cache_n) into shared memory.
+constexpr int kGroupThreads = 128;
+constexpr int kGroups = 8;
+constexpr int kUnroll = 8;  // arcs in flight per thread
+constexpr int kTableCounts = 8;  // counts below this convert by table
+
+struct PullArgs {
+    const int64_t *rowptr;
+    const int32_t *col;
+    const float *val;
+    const int32_t *tile_row;
+    int64_t ntiles;
+    int64_t nitems;
+    const int32_t *chunk_hub;
+    const int64_t *chunk_begin;
+    const int64_t *hub_ptr;
+    const int32_t *col_h;
+    const float *val_h;
+    const uint8_t *Yc;
+    const uint32_t *counts;
+    float *Z;
+    uint32_t *hub_part;
+    unsigned long long *work;
+    const DevStatus *st;
+    int32_t K;
+    int32_t max_rows;
+    int32_t cache_n;      // labels of ranks [0, cache_n) held in shared memory
+    int32_t cache_bytes;  // cache_n rounded up to 16
+    int32_t group_bytes;
+    int32_t acc_off, lab_off, val_off, slot_off;
+};
+
+__device__ __forceinline__ void group_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t label_of(const PullArgs &a,
+                                             const uint8_t *cache, int32_t v,
+                                             uint64_t keep)
+{
+    return v < a.cache_n ? (uint32_t)cache[v] : load_label(a.Yc + v, keep);
+}
+
+template <bool WEIGHTED>
+__device__ __forceinline__ float cell_value(uint32_t c, int k,
+                                            const uint32_t *nk,
+                                            const float *table)
+{
+    if (WEIGHTED)
+        return sum_to_z(__uint_as_float(c), nk[k]);
+    return c < (uint32_t)kTableCounts ? table[k * kTableCounts + c]
+                                      : count_to_z(c, nk[k]);
+}
+
+// Adds the arcs [0, NA) of a tile or chunk whose first arc is colp[0]
+// (= col + A0, any alignment): 16-byte loads of four arcs for the aligned
+// body, single arcs for the head and tail.  cell_of(i, y) gives the
+// accumulator index of arc i with label y (< 0 to skip it).
+template <bool WEIGHTED, class CellOf>
+__device__ __forceinline__ void sweep_arcs(const PullArgs &a,
+                                           const uint8_t *cache,
+                                           const int32_t *colp,
+                                           const float *valp, int NA, int gt,
+                                           uint32_t *acc, CellOf cell_of)
+{
+    const uint64_t keep = policy_evict_last();
+    float *accf = reinterpret_cast<float *>(acc);
+    const int head =
+        min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
+    auto one = [&](int i, int32_t v, float w) {
+        const uint32_t y = label_of(a, cache, v, keep);
+        if (y != kNoLabel) {
+            const int c = cell_of(i, y);
+            if (WEIGHTED)
+                atomicAdd(accf + c, w);
+            else
+                atomicAdd(acc + c, 1u);
+        }
+    };
+    if (gt < head)
+        one(gt, colp[gt], WEIGHTED ? valp[gt] : 0.0f);
+    const int nq = (NA - head) >> 2;
+    const int4 *col4 = reinterpret_cast<const int4 *>(colp + head);
+    const float4 *val4 = reinterpret_cast<const float4 *>(valp + head);
+    constexpr int kQ = kUnroll / 4;  // quads in flight per thread
+    for (int q0 = gt; q0 < nq; q0 += kQ * kGroupThreads) {
+        int4 c[kQ];
+        float4 w[kQ];
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int q = q0 + u * kGroupThreads;
+            c[u] = q < nq ? __ldcs(col4 + q) : make_int4(0, 0, 0, 0);
+            if (WEIGHTED)
+                w[u] = q < nq ? __ldcs(val4 + q) : make_float4(0, 0, 0, 0);
+        }
+        uint32_t y[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const bool ok = q0 + u * kGroupThreads < nq;
+            y[4 * u + 0] = ok ? label_of(a, cache, c[u].x, keep) : kNoLabel;
+            y[4 * u + 1] = ok ? label_of(a, cache, c[u].y, keep) : kNoLabel;
+            y[4 * u + 2] = ok ? label_of(a, cache, c[u].z, keep) : kNoLabel;
+            y[4 * u + 3] = ok ? label_of(a, cache, c[u].w, keep) : kNoLabel;
+        }
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int i0 = head + 4 * (q0 + u * kGroupThreads);
+            const float ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t yy = y[4 * u + e];
+                if (yy != kNoLabel) {
+                    const int cc = cell_of(i0 + e, yy);
+                    if (WEIGHTED)
+                        atomicAdd(accf + cc, ws[e]);
+                    else
+                        atomicAdd(acc + cc, 1u);
+                }
+            }
+        }
+    }
+    const int tail0 = head + 4 * nq;
+    if (gt < NA - tail0)
+        one(tail0 + gt, colp[tail0 + gt], WEIGHTED ? valp[tail0 + gt] : 0.0f);
+}
+
+template <bool WEIGHTED>
+__device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
+                                         unsigned char *gs,
+                                         const uint8_t *cache,
+                                         const uint32_t *nk,
+                                         const float *table, int64_t t)
+{
+    const int32_t K = a.K;
+    const int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
+    if (r0 == r1)
+        return;
+    const int NR = r1 - r0;  // <= 128, so a local row fits in a byte
+    uint8_t *row_of = gs;    // local row of every arc of the tile
+    uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
+
+    const int64_t g0 = (int64_t)r0 * K;  // first Z cell of the tile
+    const int off = (int)(g0 & 3);       // acc[off + j] holds cell g0 + j
+    const int cells = NR * K;
+    const int lane = gt & 31, warp = gt >> 5;
+    constexpr int kWarps = kGroupThreads / 32;
+
+    // setup: zero the accumulators; warp w labels the arcs of rows w, w+4,
+    // ... (lane j holds the bounds of row w + 4j)
+    {
+        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+        for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
+            acc4[c] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int64_t A0 = a.rowptr[r0];
+    const int NA = (int)(a.rowptr[r1] - A0);
+    {
+        const int myrow = warp + kWarps * lane;
+        int b = 0, e = 0;
+        if (myrow < NR) {
+            b = (int)(a.rowptr[r0 + myrow] - A0);
+            e = (int)(a.rowptr[r0 + myrow + 1] - A0);
+        }
+        for (int j = 0; warp + kWarps * j < NR; ++j) {
+            const int bj = __shfl_sync(0xffffffffu, b, j);
+            const int ej = __shfl_sync(0xffffffffu, e, j);
+            const uint8_t row = (uint8_t)(warp + kWarps * j);
+            for (int i = bj + lane; i < ej; i += 32)
+                row_of[i] = row;
+        }
+    }
+    group_sync(g);
+
+    // (A) one coalesced sweep over the tile's arcs: label from the shared
+    //     cache or through L2, then add into the arc's row accumulator
+    sweep_arcs<WEIGHTED>(a, cache, a.col + A0,
+                         WEIGHTED ? a.val + A0 : nullptr, NA, gt, acc,
+                         [&](int i, uint32_t y) {
+                             return off + (int)row_of[i] * K + (int)y;
+                         });
+    group_sync(g);
+
+    // (C) the tile's rows are contiguous in Z: scale once and stream out,
+    //     16-byte stores between an unaligned head and tail (g0 is a
+    //     multiple of K, so cell j has class j mod K)
+    float *z = a.Z + g0;
+    const int head = min((4 - off) & 3, cells);
+    if (gt < head)
+        __stcs(z + gt, cell_value<WEIGHTED>(acc[off + gt], gt % K, nk, table));
+    const int nq = (cells - head) >> 2;
+    if (gt < nq) {
+        int k = (head + 4 * gt) % K;
+        const int kstep = (4 * kGroupThreads) % K;
+        for (int q = gt; q < nq; q += kGroupThreads) {
+            const int j0 = head + 4 * q;
+            const uint4 c4 = *reinterpret_cast<const uint4 *>(acc + off + j0);
+            float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
+                const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+                float o[4];
+                int kk = k;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    o[e] = cell_value<WEIGHTED>(cs[e], kk, nk, table);
+                    if (++kk == K)
+                        kk = 0;
+                }
+                o4 = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            __stcs(reinterpret_cast<float4 *>(z + j0), o4);
+            k += kstep;
+            if (k >= K)
+                k -= K;
+        }
+    }
+    const int tail0 = head + 4 * nq;
+    if (gt < cells - tail0) {
+        const int j = tail0 + gt;
+        __stcs(z + j, cell_value<WEIGHTED>(acc[off + j], j % K, nk, table));
+    }
+}
+
+template <bool WEIGHTED>
+__device__ __forceinline__ void hub_chunk(const PullArgs &a, int g, int gt,
+                                          unsigned char *gs,
+                                          const uint8_t *cache, int64_t c)
+{
+    const int32_t K = a.K;
+    uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);  // [8][K]
+    float *accf = reinterpret_cast<float *>(acc);
+    constexpr int kWarps = kGroupThreads / 32;
+    for (int i = gt; i < kWarps * K; i += kGroupThreads)
+        acc[i] = 0u;
+    group_sync(g);
+    const int32_t h = a.chunk_hub[c];
+    const int64_t b = a.chunk_begin[c];
+    const int64_t hend = a.hub_ptr[h + 1];
+    const int64_t e = (b + kHubChunk < hend) ? b + kHubChunk : hend;
+    const int n = (int)(e - b);
+    const int warp_base = (gt >> 5) * K;
+    sweep_arcs<WEIGHTED>(a, cache, a.col_h + b,
+                         WEIGHTED ? a.val_h + b : nullptr, n, gt, acc,
+                         [&](int, uint32_t y) { return warp_base + (int)y; });
+    group_sync(g);
+    for (int k = gt; k < K; k += kGroupThreads) {
+        if (WEIGHTED) {
+            float s = 0.0f;
+            for (int w = 0; w < kWarps; ++w)
+                s += accf[w * K + k];
+            reinterpret_cast<float *>(a.hub_part)[c * K + k] = s;
+        } else {
+            uint32_t s = 0;
+            for (int w = 0; w < kWarps; ++w)
+                s += acc[w * K + k];
+            a.hub_part[c * K + k] = s;
+        }
+    }
+}
+
+template <bool WEIGHTED, int NG>
+__global__ void __launch_bounds__(NG *kGroupThreads, 1) k_pull(PullArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    if (failed(a.st))
+        return;
+    const int32_t K = a.K;
+    uint8_t *cache = sm;
+    uint32_t *nk = reinterpret_cast<uint32_t *>(sm + a.cache_bytes);
+    float *table = reinterpret_cast<float *>(nk + 256);
+    unsigned char *groups =
+        reinterpret_cast<unsigned char *>(table + 256 * kTableCounts);
+    // the CTA's copy of the most-referenced labels (16-byte copies)
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.Yc);
+        uint4 *dst = reinterpret_cast<uint4 *>(cache);
+        for (int i = threadIdx.x; i < a.cache_bytes / 16; i += blockDim.x)
+            dst[i] = src[i];
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        nk[k] = a.counts[k];
+    if (!WEIGHTED)
+        for (int i = threadIdx.x; i < K * kTableCounts; i += blockDim.x) {
+            const int k = i / kTableCounts;
+            table[i] = count_to_z((uint32_t)(i - k * kTableCounts),
+                                  a.counts[k]);
+        }
+    __syncthreads();
+    const int g = threadIdx.x / kGroupThreads;
+    const int gt = threadIdx.x - g * kGroupThreads;
+    unsigned char *gs = groups + (size_t)g * a.group_bytes;
+    long long *slot = reinterpret_cast<long long *>(gs + a.slot_off);
+    for (int it = 0;; ++it) {
+        if (gt == 0)
+            slot[it & 1] = (long long)atomicAdd(a.work, 1ull);
+        group_sync(g);
+        const int64_t item = slot[it & 1];
+        if (item >= a.nitems)
+            break;
+        if (item < a.ntiles)
+            row_tile<WEIGHTED>(a, g, gt, gs, cache, nk, table, item);
+        else
+            hub_chunk<WEIGHTED>(a, g, gt, gs, cache, item - a.ntiles);
+    }
+}
+
+// One warp per hub row: chunk partials summed in chunk order, then scaled.
+template <bool WEIGHTED>
+__global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
+                            const int32_t *__restrict__ hub_chunk0,
+                            int64_t hubs, const uint32_t *__restrict__ part,
+                            const uint32_t *__restrict__ counts, int32_t K,
+                            float *__restrict__ Z, const DevStatus *st)
+{
+    if (failed(st))
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < hubs; h += nwarps) {
+        const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
+        float *zrow = Z + (int64_t)hub_row[h] * K;
+        for (int k = lane; k < K; k += 32) {
+            if (WEIGHTED) {
+                float s = 0.0f;
+                for (int32_t c = c0; c < c1; ++c)
+                    s += __uint_as_float(part[(int64_t)c * K + k]);
+                zrow[k] = sum_to_z(s, counts[k]);
+            } else {
+                uint32_t s = 0;
+                for (int32_t c = c0; c < c1; ++c)
+                    s += part[(int64_t)c * K + k];
+                zrow[k] = count_to_z(s, counts[k]);
+            }
+        }
+    }
+}
+
+inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct PullLayout {
+    int groups;
+    size_t total;
+};
+
+// Shared-memory plan: [label cache][n_k (256)][table 256 x 8][groups...].
+PullLayout plan_pull(const Csr &g, int32_t K, bool weighted, PullArgs &a)
+{
+    const int C = row_cost(K);
+    a.max_rows = (kTileUnits + C - 1) / C;
+    const size_t rowof = align16(kMaxTileArcs);
+    // +8 cells: the offset (< 4) and the 16-byte rounding of the zeroing
+    const size_t accb = align16((size_t)(a.max_rows * K + 8) * 4);
+    a.acc_off = (int32_t)rowof;
+    a.lab_off = 0;
+    a.val_off = 0;
+    a.slot_off = (int32_t)(rowof + accb);
+    a.group_bytes = (int32_t)(a.slot_off + 16);
+    const int groups = kGroups;
+    const size_t fixed = 256 * 4 + 256 * kTableCounts * 4 +
+                         (size_t)groups * a.group_bytes;
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                               dev) != cudaSuccess)
+        optin = 227 * 1024;
+    int64_t room = (int64_t)optin - (int64_t)fixed - 256;
+    room = room < 0 ? 0 : (room & ~int64_t(15));
+    int64_t cache = g.n < room ? g.n : room;
+    a.cache_n = (int32_t)cache;
+    a.cache_bytes = (int32_t)((cache + 15) & ~int64_t(15));
+    if (a.cache_bytes > room) {  // rounding up must not overflow the plan
+        a.cache_bytes = (int32_t)room;
+        a.cache_n = (int32_t)room;
+    }
+    PullLayout L;
+    L.groups = groups;
+    L.total = (size_t)a.cache_bytes + fixed;
+    return L;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
+                      Allocator &persist, Allocator &al, Csr &g, DevStatus *st,
+                      cudaStream_t stream)
+{
+#define GEE_TRY(x)                                                             \
+    do {                                                                       \
+        cudaError_t e_ = (x);                                                  \
+        if (e_ != cudaSuccess)                                                 \
+            return e_;                                                         \
+    } while (0)
+    g.n = n;
+    g.s = s;
+    g.weighted = (w != nullptr);
+    const int sms = sm_count();
+    uint32_t *deg, *deg_main, *hub;
+    int64_t *hub_index;
+    GEE_TRY(al.alloc((void **)&deg, sizeof(uint32_t) * (n + 1)));
+    GEE_TRY(al.alloc((void **)&deg_main, sizeof(uint32_t) * (n + 1)));
+    GEE_TRY(al.alloc((void **)&hub, sizeof(uint32_t) * (n + 1)));
+    GEE_TRY(al.alloc((void **)&hub_index, sizeof(int64_t) * (n + 1)));
+    GEE_TRY(persist.alloc((void **)&g.rowptr, sizeof(int64_t) * (n + 1)));
+    GEE_TRY(persist.alloc((void **)&g.rank, sizeof(int32_t) * (n + 1)));
+    GEE_TRY(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * (n + 1), stream));
+    if (s > 0)
+        k_csr_degree<<<grid_for(s, 256, sms * 8), 256, 0, stream>>>(
+            E, w, s, n, deg, st);
+    if (n > 0)
+        k_classify<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
+            deg, n, deg_main, hub);
+    GEE_TRY(exclusive_scan(deg_main, n, g.rowptr, al, stream));
+    GEE_TRY(exclusive_scan(hub, n, hub_index, al, stream));
+    // degree ranks
+    {
+        uint32_t *bucket_count;
+        int64_t *bucket_base;
+        unsigned long long *cursor;
+        GEE_TRY(al.alloc((void **)&bucket_count, sizeof(uint32_t) * kRankBuckets));
+        GEE_TRY(al.alloc((void **)&bucket_base, sizeof(int64_t) * kRankBuckets));
+        GEE_TRY(al.alloc((void **)&cursor,
+                         sizeof(unsigned long long) * kRankBuckets));
+        GEE_TRY(cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * kRankBuckets,
+                                stream));
+        GEE_TRY(cudaMemsetAsync(cursor, 0,
+                                sizeof(unsigned long long) * kRankBuckets,
+                                stream));
+        if (n > 0) {
+            k_rank_hist<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
+                deg, n, bucket_count);
+            k_rank_base<<<1, 32, 0, stream>>>(bucket_count, bucket_base);
+            k_rank_assign<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
+                deg, n, bucket_base, cursor, g.rank);
+        }
+    }
+    int64_t host[2];
+    GEE_TRY(cudaMemcpyAsync(&host[0], g.rowptr + n, 8, cudaMemcpyDeviceToHost,
+                            stream));
+    GEE_TRY(cudaMemcpyAsync(&host[1], hub_index + n, 8,
+                            cudaMemcpyDeviceToHost, stream));
+    DevStatus hst;
+    GEE_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost,
+                            stream));
+    GEE_TRY(cudaStreamSynchronize(stream));
+    g.negative_weight = hst.aux;
+    if (hst.code != 0)
+        return cudaSuccess;  // caller reports the status
+    g.nnz_main = host[0];
+    g.hubs = host[1];
+    g.hub_arcs = 2 * s - g.nnz_main;
+    // arrays are padded by 4 entries so 16-byte vector reads may overrun
+    GEE_TRY(persist.alloc((void **)&g.col, sizeof(int32_t) * (g.nnz_main + 4)));
+    if (g.weighted)
+        GEE_TRY(persist.alloc((void **)&g.val, sizeof(float) * (g.nnz_main + 4)));
+    int64_t *base;
+    uint32_t *cursor;
+    GEE_TRY(al.alloc((void **)&base, sizeof(int64_t) * (n + 1)));
+    GEE_TRY(al.alloc((void **)&cursor, sizeof(uint32_t) * (n + 1)));
+    GEE_TRY(persist.alloc((void **)&g.hub_ptr, sizeof(int64_t) * (g.hubs + 1)));
+    if (g.hubs > 0) {
+        uint32_t *hub_deg, *hub_nchunks;
+        GEE_TRY(persist.alloc((void **)&g.hub_row, sizeof(int32_t) * g.hubs));
+        GEE_TRY(al.alloc((void **)&hub_deg, sizeof(uint32_t) * g.hubs));
+        GEE_TRY(al.alloc((void **)&hub_nchunks, sizeof(uint32_t) * g.hubs));
+        GEE_TRY(persist.alloc((void **)&g.hub_chunk0,
+                              sizeof(int32_t) * (g.hubs + 1)));
+        GEE_TRY(persist.alloc((void **)&g.col_h,
+                              sizeof(int32_t) * (g.hub_arcs + 4)));
+        if (g.weighted)
+            GEE_TRY(persist.alloc((void **)&g.val_h,
+                                  sizeof(float) * (g.hub_arcs + 4)));
+        k_hub_list<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
+            deg, hub, hub_index, n, g.hub_row, hub_deg, hub_nchunks);
+        GEE_TRY(exclusive_scan(hub_deg, g.hubs, g.hub_ptr, al, stream));
+        GEE_TRY(exclusive_scan(hub_nchunks, g.hubs, g.hub_chunk0, al, stream));
+        int32_t chunks = 0;
+        GEE_TRY(cudaMemcpyAsync(&chunks, g.hub_chunk0 + g.hubs, 4,
+                                cudaMemcpyDeviceToHost, stream));
+        GEE_TRY(cudaStreamSynchronize(stream));
+        g.chunks = chunks;
+        GEE_TRY(persist.alloc((void **)&g.chunk_hub, sizeof(int32_t) * chunks));
+        GEE_TRY(persist.alloc((void **)&g.chunk_begin,
+                              sizeof(int64_t) * chunks));
+        k_chunk_list<<<grid_for(g.hubs, 128, sms * 8), 128, 0, stream>>>(
+            g.hub_ptr, g.hub_chunk0, g.hubs, g.chunk_hub, g.chunk_begin);
+    } else {
+        GEE_TRY(cudaMemsetAsync(g.hub_ptr, 0, sizeof(int64_t), stream));
+    }
+    if (n > 0)
+        k_base<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
+            g.rowptr, hub, hub_index, g.hub_ptr, n, base);
+    GEE_TRY(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * (n + 1), stream));
+    if (s > 0)
+        k_csr_fill<<<grid_for(s, 256, sms * 8), 256, 0, stream>>>(
+            E, w, s, base, g.rank, cursor, g.col, g.val, g.col_h, g.val_h, st);
+    return cudaGetLastError();
+#undef GEE_TRY
+}
+
+cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
+                                   cudaStream_t stream)
+{
+    const int sms = sm_count();
+    float *r, *r_rank;
+    cudaError_t e = tmp.alloc((void **)&r, sizeof(float) * (g.n + 1));
+    if (e != cudaSuccess)
+        return e;
+    e = tmp.alloc((void **)&r_rank, sizeof(float) * (g.n + 1));
+    if (e != cudaSuccess)
+        return e;
+    e = persist.alloc((void **)&g.lap_val, sizeof(float) * (g.nnz_main + 4));
+    if (e != cudaSuccess)
+        return e;
+    if (g.hubs > 0) {
+        e = persist.alloc((void **)&g.lap_val_h,
+                          sizeof(float) * (g.hub_arcs + 4));
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (g.n > 0) {
+        k_row_rsqrt<<<grid_for(g.n, 256, sms * 8), 256, 0, stream>>>(
+            g.rowptr, g.val, g.n, r);
+        if (g.hubs > 0)
+            k_hub_rsqrt<<<grid_for(g.hubs * 32, 256, sms * 8), 256, 0,
+                          stream>>>(g.hub_row, g.hub_ptr, g.val_h, g.hubs, r);
+        k_scatter_by_rank<<<grid_for(g.n, 256, sms * 8), 256, 0, stream>>>(
+            r, g.n, g.rank, r_rank);
+        k_lap_values<<<grid_for(g.n, 256, sms * 8), 256, 0, stream>>>(
+            g.rowptr, g.col, g.val, g.n, r, r_rank, g.lap_val);
+        if (g.hubs > 0)
+            k_lap_values_hub<<<grid_for(g.hubs * 32, 256, sms * 8), 256, 0,
+                               stream>>>(g.hub_row, g.hub_ptr, g.col_h,
+                                         g.val_h, g.hubs, r, r_rank,
+                                         g.lap_val_h);
+    }
+    return cudaGetLastError();
+}
+
+int64_t pull_tiles(const Csr &g, int32_t K)
+{
+    const int64_t units = g.nnz_main + g.n * (int64_t)row_cost(K);
+    return (units + kTileUnits - 1) / kTileUnits;
+}
+
+cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
+                             int64_t ntiles, cudaStream_t stream)
+{
+    k_partition<<<grid_for(ntiles + 1, 256, 1 << 30), 256, 0, stream>>>(
+        g.rowptr, g.n, K, ntiles, tile_row);
+    return cudaGetLastError();
+}
+
+template <bool W, int NG>
+static cudaError_t pull_launch_t(const PullArgs &a, size_t smem,
+                                 cudaStream_t stream)
+{
+    cudaError_t e = cudaFuncSetAttribute(
+        k_pull<W, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_pull<W, NG><<<sm_count(), NG * kGroupThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull(const Csr &g, int32_t K, bool weighted,
+                        bool laplacian, const int32_t *tile_row,
+                        int64_t ntiles, const uint8_t *Yc,
+                        const uint32_t *counts, float *Z, void *hub_part,
+                        unsigned long long *work, const DevStatus *st,
+                        cudaStream_t stream)
+{
+    PullArgs a;
+    a.rowptr = g.rowptr;
+    a.col = g.col;
+    a.val = laplacian ? g.lap_val : g.val;
+    a.tile_row = tile_row;
+    a.ntiles = ntiles;
+    a.nitems = ntiles + g.chunks;
+    a.chunk_hub = g.chunk_hub;
+    a.chunk_begin = g.chunk_begin;
+    a.hub_ptr = g.hub_ptr;
+    a.col_h = g.col_h;
+    a.val_h = laplacian ? g.lap_val_h : g.val_h;
+    a.Yc = Yc;
+    a.counts = counts;
+    a.Z = Z;
+    a.hub_part = static_cast<uint32_t *>(hub_part);
+    a.work = work;
+    a.st = st;
+    a.K = K;
+    const bool wpath = weighted || laplacian;
+    const PullLayout L = plan_pull(g, K, wpath, a);
+    if (a.nitems == 0)
+        return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess)
+        return e;
+    return wpath ? pull_launch_t<true, kGroups>(a, L.total, stream)
+                 : pull_launch_t<false, kGroups>(a, L.total, stream);
+}
+
+cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
+                             bool laplacian, const uint32_t *counts, float *Z,
+                             const void *hub_part, const DevStatus *st,
+                             cudaStream_t stream)
+{
+    if (g.hubs == 0)
+        return cudaSuccess;
+    const uint32_t *part = static_cast<const uint32_t *>(hub_part);
+    const int fb = grid_for(g.hubs * 32, 256, sm_count() * 8);
+    if (weighted || laplacian)
+        k_hub_fixup<true><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
+                                                  g.hubs, part, counts, K, Z,
+                                                  st);
+    else
+        k_hub_fixup<false><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
+                                                   g.hubs, part, counts, K, Z,
+                                                   st);
+    return cudaGetLastError();
+}
+
+}  // namespace gee

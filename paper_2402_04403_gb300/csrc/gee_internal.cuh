@@ -1,0 +1,223 @@
+// gee_internal.cuh -- shared device helpers and kernel launchers of libgee.
+//
+// Layout in device memory (see gee.h for the public contract):
+//   Yc      uint8 [n]       compact labels, 255 = class unknown
+//   counts  uint32 [K]      class sizes n_k
+//   Z       float  [n][K]   row-major; the ATOMIC/PRIVATE count path uses the
+//                           same bytes as uint32 counts before finalising
+//   CSR     int64 rowptr[n+1], int32 col[], float val[] (resident graphs)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gee.h"
+
+namespace gee {
+
+constexpr uint32_t kNoLabel = 255;
+constexpr int kMaxClasses = GEE_MAX_CLASSES;
+// Row tiles of the pull pass cover kTileUnits "merged units": one unit per
+// arc plus max(K, 16) units per row (the row's Z write), so that every tile
+// moves about the same number of bytes.  Rows with more than kHubDegree arcs
+// are processed apart, in chunks of kHubChunk arcs.
+constexpr int kTileUnits = 2048;
+constexpr int kHubDegree = GEE_HUB_DEGREE;
+constexpr int kHubChunk = 2048;
+constexpr int kMaxTileArcs = kTileUnits + kHubDegree;
+
+// First error a kernel saw.  `index` is the smallest offending element.
+struct DevStatus {
+    int32_t code;
+    int32_t aux;
+    unsigned long long index;
+};
+
+__device__ __forceinline__ void report(DevStatus *st, int code,
+                                       unsigned long long index)
+{
+    atomicCAS(&st->code, 0, code);
+    atomicMin(&st->index, index);
+}
+
+__device__ __forceinline__ bool failed(const DevStatus *st)
+{
+    return *reinterpret_cast<const volatile int32_t *>(&st->code) != 0;
+}
+
+// L2 eviction policies (PTX createpolicy): labels are gathered at random and
+// should stay in L2; edges, arcs and Z rows stream through once.
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint32_t load_label(const uint8_t *p, uint64_t pol)
+{
+    uint32_t r;
+    asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;"
+        : "=r"(r)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+// Z value of a class count: RN32(c / n_k).  Exact float division when both
+// operands are below 2^24 (exactly representable); otherwise the quotient is
+// formed in double and rounded once more to float.
+__device__ __forceinline__ float count_to_z(uint32_t c, uint32_t nk)
+{
+    if (c == 0u)
+        return 0.0f;
+    if ((c | nk) < (1u << 24))
+        return __fdiv_rn(static_cast<float>(c), static_cast<float>(nk));
+    return __double2float_rn(
+        __ddiv_rn(static_cast<double>(c), static_cast<double>(nk)));
+}
+
+// Weighted/Laplacian cell: accumulated weight sum divided by n_k.
+__device__ __forceinline__ float sum_to_z(float acc, uint32_t nk)
+{
+    if (nk == 0u)
+        return 0.0f;
+    return __fdiv_rn(acc, static_cast<float>(nk));
+}
+
+inline int grid_for(int64_t work, int threads, int max_blocks)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1)
+        b = 1;
+    if (b > max_blocks)
+        b = max_blocks;
+    return static_cast<int>(b);
+}
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `stream` and return cudaGetLastError().
+
+cudaError_t launch_status_init(DevStatus *st, cudaStream_t stream);
+
+// S1 + S2: validate labels, write compact labels, class histogram.
+// counts must be zeroed by the caller.  With rank != null the compact label
+// of node i goes to Yc[rank[i]] (rank order), else to Yc[i].
+cudaError_t launch_labels(const int32_t *Y, int64_t n, int32_t K,
+                          const int32_t *rank, uint8_t *Yc, uint32_t *counts,
+                          DevStatus *st, cudaStream_t stream);
+
+cudaError_t launch_validate_edges(const int32_t *E, int64_t s, int64_t n,
+                                  DevStatus *st, cudaStream_t stream);
+
+// S3 (edge-list form): d[u] += w for both endpoints, checks endpoints and the
+// sign of weights; then r[u] = 1/sqrt(d[u]) (0 for d = 0).
+cudaError_t launch_degree(const int32_t *E, const float *w, int64_t s,
+                          int64_t n, double *d, DevStatus *st,
+                          cudaStream_t stream);
+cudaError_t launch_rsqrt(const double *d, int64_t n, float *r,
+                         const DevStatus *st, cudaStream_t stream);
+
+cudaError_t launch_zero(void *p, int64_t words, const DevStatus *st,
+                        cudaStream_t stream);
+
+// S4 (edge-list form).  Count path: C (uint32, same bytes as Z) += 1.
+// Weighted path: Z += w (times r of the sending node for the Laplacian).
+cudaError_t launch_scatter_atomic(const int32_t *E, const float *w,
+                                  const float *r, int64_t s, int64_t n,
+                                  int32_t K, const uint8_t *Yc, void *Z,
+                                  bool check_nodes, int threads, DevStatus *st,
+                                  cudaStream_t stream);
+cudaError_t launch_scatter_private(const int32_t *E, const float *w,
+                                   const float *r, int64_t s, int64_t n,
+                                   int32_t K, const uint8_t *Yc, void *Z,
+                                   bool check_nodes, int threads,
+                                   DevStatus *st, cudaStream_t stream);
+int64_t private_cells_limit();
+
+// S5 (edge-list form), in place over Z.
+cudaError_t launch_finalize_count(void *Z, int64_t n, int32_t K,
+                                  const uint32_t *counts, const DevStatus *st,
+                                  cudaStream_t stream);
+cudaError_t launch_finalize_weighted(float *Z, const float *r, int64_t n,
+                                     int32_t K, const uint32_t *counts,
+                                     const DevStatus *st, cudaStream_t stream);
+
+// ------------------------------------------------------------ CSR (gee_csr)
+struct Csr {
+    int64_t n = 0, s = 0;
+    int64_t nnz_main = 0;       // arcs of non-hub rows
+    int64_t hubs = 0;           // rows with more than kHubDegree arcs
+    int64_t chunks = 0;         // hub chunks of <= kHubChunk arcs
+    int64_t hub_arcs = 0;
+    bool weighted = false;
+    int32_t negative_weight = 0;
+    int64_t *rowptr = nullptr;      // [n+1], hub rows empty
+    int32_t *rank = nullptr;        // [n] degree rank of each node
+    int32_t *col = nullptr;         // [nnz_main + pad] target ranks
+    float *val = nullptr;           // [nnz_main + pad] or null
+    int32_t *hub_row = nullptr;     // [hubs]
+    int64_t *hub_ptr = nullptr;     // [hubs+1] into col_h
+    int32_t *col_h = nullptr;       // [hub_arcs + pad]
+    float *val_h = nullptr;
+    int32_t *chunk_hub = nullptr;   // [chunks]
+    int64_t *chunk_begin = nullptr; // [chunks]
+    int32_t *hub_chunk0 = nullptr;  // [hubs+1] first chunk of each hub
+    float *lap_val = nullptr;       // Laplacian arc values (lazy)
+    float *lap_val_h = nullptr;
+};
+
+// Allocation callback used by the CSR builder (pool or cudaMalloc).
+struct Allocator {
+    virtual cudaError_t alloc(void **p, size_t bytes) = 0;
+    virtual ~Allocator() {}
+};
+
+// Builds the symmetric CSR of an edge list (validating endpoints into st).
+// `persist` provides the arrays kept in g, `tmp` the scratch.  Synchronises
+// the stream (twice) to size the arrays.
+cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
+                      Allocator &persist, Allocator &tmp, Csr &g,
+                      DevStatus *st, cudaStream_t stream);
+
+// Laplacian arc values w / sqrt(d_u d_v) from the CSR's row sums.
+cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
+                                   cudaStream_t stream);
+
+// Row-tile partition for K: tile_row[ntiles+1].
+int64_t pull_tiles(const Csr &g, int32_t K);
+cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
+                             int64_t ntiles, cudaStream_t stream);
+
+// S4 + S5 (CSR form): writes every row of Z exactly once; hub rows get
+// zeros here and their values from launch_hub_fixup, which must follow.
+// Yc is in rank order.  hub_part: scratch [chunks * K] of 4-byte per-chunk
+// partial sums; work: one 8-byte scratch counter.
+cudaError_t launch_pull(const Csr &g, int32_t K, bool weighted,
+                        bool laplacian, const int32_t *tile_row,
+                        int64_t ntiles, const uint8_t *Yc,
+                        const uint32_t *counts, float *Z, void *hub_part,
+                        unsigned long long *work, const DevStatus *st,
+                        cudaStream_t stream);
+cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
+                             bool laplacian, const uint32_t *counts, float *Z,
+                             const void *hub_part, const DevStatus *st,
+                             cudaStream_t stream);
+
+// ------------------------------------------------------------ tracing
+// When tracing is on (gee_profile_enable), a ProfScope brackets one kernel
+// launch with CUDA events on the launching stream.
+class ProfScope {
+  public:
+    ProfScope(const char *name, cudaStream_t stream);
+    ~ProfScope();
+
+  private:
+    const char *name_;
+    cudaStream_t stream_;
+    cudaEvent_t begin_ = nullptr;
+};
+
+}  // namespace gee

@@ -1,0 +1,84 @@
+"""The C ABI loads and exports what include/gee.h declares (no GPU needed).
+
+Only host-side logic runs here: symbol lookup, status strings, option
+defaults and argument checks that return before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gee.h")
+
+
+@pytest.fixture(scope="module")
+def gee():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_04403_gb300 as gee
+    return gee
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"GEE_API\s+[\w\s\*]*?\b(gee_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gee_histogram", "gee_embed", "gee_graph_create",
+                     "gee_embed_graph", "gee_graph_destroy", "gee_workspace_bytes",
+                     "gee_status_string", "gee_embed_host", "gee_embed_graph_host"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(gee):
+    handle = ctypes.CDLL(os.path.join(ROOT, "paper_2402_04403_gb300", "libgee.so"))
+    for name in declared_functions():
+        assert hasattr(handle, name), f"{name} missing from libgee.so"
+    from paper_2402_04403_gb300 import _lib
+    assert set(_lib.SIGNATURES) >= set(declared_functions())
+
+
+def test_generator_and_oracle_libraries_load():
+    import graphgen
+    import oracle
+    g = ctypes.CDLL(graphgen.build())
+    for name in ("graphgen_rmat", "graphgen_labels", "graphgen_weights"):
+        assert hasattr(g, name)
+    o = ctypes.CDLL(oracle.build())
+    for name in ("gee_oracle_embed", "gee_oracle_counts", "gee_oracle_embed_rows"):
+        assert hasattr(o, name)
+
+
+def test_status_strings(gee):
+    assert gee.status_string(0) == "ok"
+    assert "label" in gee.status_string(gee.STATUS["GEE_ERR_LABEL_RANGE"])
+    assert gee.status_string(99) == "unknown status"
+
+
+def test_default_options(gee):
+    from paper_2402_04403_gb300 import _lib
+    o = _lib.Options()
+    _lib.lib().gee_options_default(ctypes.byref(o))
+    assert (o.strategy, o.validate_edges, o.private_max_cells, o.block) == (0, 1, 0, 0)
+
+
+def test_argument_checks_return_before_any_device_work(gee):
+    lib = gee.load()
+    null = ctypes.c_void_p()
+    # K out of range, negative sizes, bad block: no CUDA call is made
+    assert lib.gee_embed(null, null, 0, null, 0, 0, 0, null, None, null) == 1
+    assert lib.gee_embed(null, null, 0, null, 0, 256, 0, null, None, null) == 8
+    assert lib.gee_embed(null, null, -1, null, 0, 2, 0, null, None, null) == 1
+    assert lib.gee_embed(null, null, 5, null, 4, 2, 0, null, None, null) == 1  # NULL edges
+    assert lib.gee_histogram(null, 10, 3, null, null) == 1
+    assert lib.gee_histogram(null, 0, 0, null, null) == 1
+    out = ctypes.c_void_p()
+    assert lib.gee_graph_create(null, null, 3, 10, null, ctypes.byref(out)) == 1
+    assert lib.gee_embed_graph(null, null, 3, 0, null, None, null) == 1
+    lib.gee_graph_destroy(null)  # no-op
+    o = gee._lib.options(block=48)
+    assert lib.gee_embed(null, null, 0, null, 0, 2, 0, null, ctypes.byref(o), null) == 1

@@ -1,0 +1,217 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Unit weights without the Laplacian: bit-exact against RN32(C / n_k).
+Float weights and the Laplacian variant: |Z - Z64| <= 1e-5 |Z64| wherever
+Z64 != 0 and Z == 0 exactly where Z64 == 0 (all weights are positive, so no
+cancellation); the largest relative and absolute errors are printed.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import _pins
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+STRATEGIES = ["atomic", "private", "segmented"]
+
+
+@pytest.fixture(scope="module")
+def gee():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_04403_gb300 as gee
+    gee.load()
+    return gee
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def assert_weighted_close(got, want, what=""):
+    got = np.asarray(got, np.float64)
+    nz = want != 0
+    assert np.all(got[~nz] == 0), f"{what}: nonzero where the oracle has 0"
+    if nz.any():
+        rel = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+        worst = rel.max()
+        print(f"{what}: max rel err {worst:.3e}, max abs err "
+              f"{np.abs(got - want).max():.3e}")
+        assert worst <= REL_TOL, f"{what}: rel err {worst:.3e} > {REL_TOL}"
+
+
+def run_all_paths(gee, edges, Y, K, weights=None, laplacian=False, strategies=STRATEGIES):
+    """Z from every edge-list strategy and from a resident graph."""
+    e_d, y_d = _dev(edges.reshape(-1, 2)), _dev(Y)
+    w_d = None if weights is None else _dev(weights)
+    out = {}
+    for st in strategies:
+        out[st] = gee.embed(e_d, y_d, K, weights=w_d, laplacian=laplacian,
+                            strategy=st).cpu().numpy()
+    with gee.Graph(e_d, Y.size, weights=w_d) as g:
+        out["graph"] = g.embed(y_d, K, laplacian=laplacian).cpu().numpy()
+    return out
+
+
+def check_case(gee, edges, Y, K, weights=None, laplacian=False, what=""):
+    edges = np.asarray(edges, np.int32).reshape(-1, 2)
+    Y = np.asarray(Y, np.int32)
+    outs = run_all_paths(gee, edges, Y, K, weights, laplacian)
+    if weights is None and not laplacian:
+        want = oracle.embed_counts32(edges, Y, K)
+        for name, got in outs.items():
+            assert got.dtype == np.float32
+            mism = np.argwhere(got != want)
+            assert mism.size == 0, f"{what}/{name}: {len(mism)} cells differ, first {mism[:3]}"
+    else:
+        want = oracle.embed(edges, Y, K, weights=weights, laplacian=laplacian)
+        for name, got in outs.items():
+            assert_weighted_close(got, want, f"{what}/{name}")
+
+
+@pytest.mark.parametrize("case", _pins.load_hand_cases(), ids=lambda c: c["name"])
+def test_hand_cases(gee, case):
+    w = None if case["weights"] is None else np.asarray(case["weights"], np.float32)
+    check_case(gee, case["edges"], case["Y"], case["K"], w, case["laplacian"], case["name"])
+
+
+def test_tiny_sbm_count_path_bit_exact(gee, tiny_sbm_graph):
+    edges, Y = tiny_sbm_graph
+    check_case(gee, edges, Y, 5, what="sbm")
+
+
+def test_tiny_sbm_weighted_and_laplacian(gee, tiny_sbm_graph):
+    edges, Y = tiny_sbm_graph
+    w = graphgen.weights(edges.shape[0], seed=11)
+    check_case(gee, edges, Y, 5, weights=w, what="sbm-w")
+    check_case(gee, edges, Y, 5, laplacian=True, what="sbm-lap")
+    check_case(gee, edges, Y, 5, weights=w, laplacian=True, what="sbm-w-lap")
+
+
+RANDOM_CASES = [
+    # n, s, K, frac_unlabeled
+    (1, 0, 1, 0.0),
+    (1, 5, 3, 0.0),          # all self-loops on one node
+    (2, 1, 2, 0.5),
+    (37, 1001, 5, 0.3),      # ragged: odd edge count, n*K not a multiple of 4
+    (1000, 3, 50, 0.1),      # mostly isolated nodes
+    (5000, 50001, 20, 0.1),  # several row tiles, ragged tail
+    (3001, 40000, 255, 0.0), # K at its maximum
+    (4000, 30000, 1, 0.0),   # K = 1
+    (500, 20000, 7, 1.0),    # nothing labelled
+]
+
+
+@pytest.mark.parametrize("n,s,K,frac", RANDOM_CASES)
+@pytest.mark.parametrize("weighted", [False, True])
+def test_random_multigraphs(gee, n, s, K, frac, weighted):
+    edges = graphgen.random_graph(n, s, seed=n * 7 + s)
+    Y = graphgen.labels(n, K, seed=n + K, frac_unlabeled=frac)
+    w = graphgen.weights(s, seed=s + 3) if weighted else None
+    check_case(gee, edges, Y, K, weights=w, what=f"rand{n}x{s}")
+    if weighted:
+        check_case(gee, edges, Y, K, weights=w, laplacian=True, what=f"rand{n}x{s}-lap")
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    """R-MAT scale 16, 2^20 edges: hubs far above the 4096-arc hub threshold."""
+    n = 1 << 16
+    edges = graphgen.rmat_edges(16, n, 0, 1 << 20, seed=21)
+    deg = np.bincount(edges.ravel(), minlength=n)
+    assert deg.max() > 4 * 4096
+    return edges, n
+
+
+@pytest.mark.parametrize("K,frac", [(20, 0.1), (50, 0.0), (3, 0.5)])
+def test_rmat_with_hub_rows(gee, rmat16, K, frac):
+    edges, n = rmat16
+    Y = graphgen.labels(n, K, seed=K, frac_unlabeled=frac)
+    check_case(gee, edges, Y, K, what=f"rmat16-K{K}")
+
+
+def test_rmat_weighted_with_hub_rows(gee, rmat16):
+    edges, n = rmat16
+    K = 20
+    Y = graphgen.labels(n, K, seed=99, frac_unlabeled=0.1)
+    w = graphgen.weights(edges.shape[0], seed=98)
+    check_case(gee, edges, Y, K, weights=w, what="rmat16-w")
+    check_case(gee, edges, Y, K, weights=w, laplacian=True, what="rmat16-w-lap")
+
+
+def test_unaligned_device_pointers(gee):
+    """Edge and label arrays that start off a 16-byte boundary take the
+    scalar paths of the streaming kernels."""
+    import torch
+    n, s, K = 777, 9999, 6
+    edges = graphgen.random_graph(n, s, seed=5)
+    Y = graphgen.labels(n, K, seed=6, frac_unlabeled=0.2)
+    big_e = torch.zeros((s + 1, 2), dtype=torch.int32, device="cuda")
+    big_e[1:] = _dev(edges)
+    big_y = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    big_y[1:] = _dev(Y)
+    e_d, y_d = big_e[1:], big_y[1:]
+    assert e_d.data_ptr() % 16 != 0 and y_d.data_ptr() % 16 != 0
+    want = oracle.embed_counts32(edges, Y, K)
+    for st in STRATEGIES:
+        got = gee.embed(e_d, y_d, K, strategy=st).cpu().numpy()
+        assert np.array_equal(got, want), st
+    out = torch.full((n * K + 1,), 7.0, device="cuda")[1:].view(n, K)
+    got = gee.embed(e_d, y_d, K, strategy="atomic", out=out).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_repeated_calls(gee, tiny_sbm_graph):
+    """Unit weights: every call gives the same bits.  Float weights: the
+    shared-memory float atomics may add in a different order from call to
+    call, so repeated results agree to the stated tolerance, not bitwise."""
+    import torch
+    edges, Y = tiny_sbm_graph
+    e_d, y_d = _dev(edges), _dev(Y)
+    w_d = _dev(graphgen.weights(edges.shape[0], seed=2))
+    with gee.Graph(e_d, Y.size) as g:
+        assert torch.equal(g.embed(y_d, 5), g.embed(y_d, 5))
+    with gee.Graph(e_d, Y.size, weights=w_d) as g:
+        a = g.embed(y_d, 5).cpu().numpy()
+        b = g.embed(y_d, 5).cpu().numpy()
+        assert_weighted_close(a, b.astype(np.float64), "repeat-weighted")
+    c = gee.embed(e_d, y_d, 5, strategy="atomic")
+    d = gee.embed(e_d, y_d, 5, strategy="atomic")
+    assert torch.equal(c, d)
+
+
+def test_histogram(gee):
+    n, K = 100003, 37
+    Y = graphgen.labels(n, K, seed=8, frac_unlabeled=0.25)
+    got = gee.histogram(_dev(Y), K).cpu().numpy()
+    assert np.array_equal(got, oracle.class_counts(Y, K))
+
+
+def test_host_entry_points(gee, tiny_sbm_graph):
+    edges, Y = tiny_sbm_graph
+    want = oracle.embed_counts32(edges, Y, 5)
+    got = gee.embed_host(edges, Y, 5)
+    assert np.array_equal(got, want)
+    with gee.Graph(_dev(edges), Y.size) as g:
+        assert np.array_equal(g.embed_host(Y, 5), want)
+        info = g.info()
+        assert info["n"] == Y.size and info["s"] == edges.shape[0]
+
+
+def test_relabeling_a_resident_graph(gee, rmat16):
+    """Many label vectors on one resident graph, each equal to its own
+    oracle result (the unsupervised-GEE re-labeling loop)."""
+    edges, n = rmat16
+    with gee.Graph(_dev(edges), n) as g:
+        for seed in range(3):
+            K = 4 + 7 * seed
+            Y = graphgen.labels(n, K, seed=1000 + seed, frac_unlabeled=0.1 * seed)
+            got = g.embed(_dev(Y), K).cpu().numpy()
+            assert np.array_equal(got, oracle.embed_counts32(edges, Y, K))
