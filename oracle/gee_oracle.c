@@ -11,8 +11,8 @@
  *
  * Conventions (readings of the paper, each one listed in the design notes):
  *   - Edge list E is s rows of (u, v) int32 node ids, row-major (s x 2), with
- *     an optional float32 weight per edge; no weights means unit weights
- *     (Section II, "Unweighted graphs have unit weights").
+ *     an optional float32 weight per edge; no weights means every edge
+ *     weighs 1 (Section II).
  *   - Labels Y are int32: classes 0..K-1 and -1 for "class unknown".  The paper
  *     writes Y in {0..K} with 0 = unknown and classes 1..K (Alg. 1 input and
  *     the comment in its W-initialisation loop); -1/0..K-1 is the same
