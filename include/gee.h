@@ -173,6 +173,32 @@ GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
                            const gee_options *opts);
 
 /*
+ * Allocation-free edge-list embedding.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory once
+ * they are running -- for example a service whose device memory was divided
+ * up at start-up by another allocator, or latency-critical code that must
+ * not call into the driver's allocator mid-flight.
+ *
+ * Same result as gee_embed(edges, weights, s, Y, n, K, laplacian = 0, Z)
+ * with the ATOMIC strategy and endpoint validation on, but it allocates
+ * nothing: its scratch (status word, n_k, compact labels) lives in one fixed
+ * array of GEE_NOALLOC_SCRATCH_BYTES in device global memory that belongs to
+ * the library image, so every GPU that loads libgee holds those bytes until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (once per device); make that first call before any stream
+ * capture.  n above GEE_NOALLOC_MAX_NODES returns GEE_ERR_UNSUPPORTED.  The
+ * array is shared by all calls and keeps the last call's contents (each call
+ * clears what must start at zero), so calls whose work overlaps on the GPU
+ * race on it: run them one at a time.  No Laplacian variant.
+ */
+#define GEE_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define GEE_NOALLOC_MAX_NODES (GEE_NOALLOC_SCRATCH_BYTES - 2048u)
+GEE_API gee_status gee_embed_noalloc(const int32_t *edges,
+                                     const float *weights, int64_t s,
+                                     const int32_t *Y, int64_t n, int32_t K,
+                                     float *Z, gee_stream_t stream);
+
+/*
  * Tracing.  While enabled (process-wide), every kernel launch of the library
  * is bracketed by two CUDA events on the stream it is launched on.
  * gee_profile_read waits for the recorded events, fills up to max_entries

@@ -15,13 +15,13 @@ from __future__ import annotations
 
 import ctypes
 
-from ._lib import (GeeError, HUB_DEGREE, MAX_CLASSES, STATUS, STATUS_NAMES,
+from ._lib import (GeeError, HUB_DEGREE, MAX_CLASSES, NOALLOC_MAX_NODES, STATUS, STATUS_NAMES,
                    STRATEGIES, STRATEGY_NAMES, KernelTime, check, lib, options)
 
 __all__ = ["GeeError", "Graph", "embed", "embed_host", "histogram",
            "pick_strategy", "workspace_bytes", "status_string", "STATUS",
            "STRATEGIES", "MAX_CLASSES", "HUB_DEGREE", "load", "profile_enable",
-           "profile_read"]
+           "profile_read", "embed_noalloc", "NOALLOC_MAX_NODES"]
 
 
 def load():
@@ -122,6 +122,25 @@ def embed(edges, Y, K: int, weights=None, laplacian: bool = False, *,
         _dev_ptr(out, torch.float32, "out", (n, K)), ctypes.byref(o),
         _stream_handle(stream))
     check(rc, "gee_embed")
+    return out
+
+
+def embed_noalloc(edges, Y, K: int, weights=None, *, out=None, stream=None):
+    """gee_embed_noalloc: the edge-list embedding with the library's fixed
+    scratch array instead of any device allocation (for callers that cannot
+    allocate once running).  ``out`` should be preallocated by such callers.
+    Calls must not overlap on the GPU."""
+    torch = _torch()
+    s = _edges_shape(edges)
+    n = Y.numel()
+    if out is None:
+        out = torch.empty((n, K), dtype=torch.float32, device=Y.device)
+    rc = lib().gee_embed_noalloc(
+        _dev_ptr(edges, torch.int32, "edges"),
+        _dev_ptr(weights, torch.float32, "weights", (s,)), s,
+        _dev_ptr(Y, torch.int32, "Y", (n,)), n, int(K),
+        _dev_ptr(out, torch.float32, "out", (n, K)), _stream_handle(stream))
+    check(rc, "gee_embed_noalloc")
     return out
 
 

@@ -25,6 +25,7 @@ STATUS = {v: k for k, v in STATUS_NAMES.items()}
 STRATEGIES = {"auto": 0, "atomic": 1, "private": 2, "segmented": 3}
 STRATEGY_NAMES = {v: k for k, v in STRATEGIES.items()}
 MAX_CLASSES = 255
+NOALLOC_MAX_NODES = (16 << 20) - 2048
 HUB_DEGREE = 4096
 
 
@@ -79,6 +80,7 @@ SIGNATURES = {
     "gee_graph_destroy": (None, [_P]),
     "gee_pick_strategy": (ctypes.c_int, [_I64, _I64, _I32, _OPT]),
     "gee_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I32, _I32, _I32, _OPT]),
+    "gee_embed_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
     "gee_profile_enable": (None, [_I32]),
     "gee_profile_read": (_I32, [ctypes.POINTER(KernelTime), _I32]),
 }
