@@ -139,7 +139,7 @@ GEE_API gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h
  * and the sort.  Validates endpoints (GEE_ERR_NODE_RANGE, no graph).
  * edges/weights are device pointers and are not referenced after return.
  */
-#define GEE_HUB_DEGREE 4096
+#define GEE_HUB_DEGREE 128
 typedef struct gee_graph gee_graph;
 
 GEE_API gee_status gee_graph_create(const int32_t *edges, const float *weights,
@@ -156,9 +156,12 @@ GEE_API gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
                                 int32_t K, int32_t laplacian, float *Z_h,
                                 const gee_options *opts, gee_stream_t stream);
 
-/* Sizes of a resident graph; any output pointer may be NULL. */
-GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
-                          int64_t *hub_rows, int64_t *device_bytes);
+/* Sizes of a resident graph: nodes, edges, rows kept in the hub CSR (more
+ * than GEE_HUB_DEGREE arcs), their arcs, device bytes held.  Any output
+ * pointer may be NULL. */
+GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n,
+                                  int64_t *s, int64_t *hub_rows,
+                                  int64_t *hub_arcs, int64_t *device_bytes);
 
 /* Frees the graph after all device work has finished.  NULL is a no-op. */
 GEE_API void gee_graph_destroy(gee_graph *graph);

@@ -215,10 +215,11 @@ class Graph:
         return self._h
 
     def info(self) -> dict:
-        vals = [ctypes.c_int64() for _ in range(4)]
+        vals = [ctypes.c_int64() for _ in range(5)]
         check(lib().gee_graph_info(self.handle, *[ctypes.byref(v) for v in vals]),
               "gee_graph_info")
-        return dict(zip(("n", "s", "hub_rows", "device_bytes"), (v.value for v in vals)))
+        return dict(zip(("n", "s", "hub_rows", "hub_arcs", "device_bytes"),
+                        (v.value for v in vals)))
 
     def embed(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
         torch = _torch()

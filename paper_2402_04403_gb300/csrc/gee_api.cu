@@ -208,11 +208,16 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         ProfScope p("k_partition", stream);
         GEE_CHECK_CUDA(launch_partition(g, K, tile_row, ntiles, stream));
     }
-    if (ntiles + g.chunks > 0) {
-        ProfScope p("k_pull", stream);
-        GEE_CHECK_CUDA(launch_pull(g, K, g.weighted, laplacian, tile_row,
-                                   ntiles, Yc, counts, Z, hub_part, work, st,
-                                   stream));
+    {
+        ProfScope p("k_pull_light", stream);
+        GEE_CHECK_CUDA(launch_pull_light(g, K, g.weighted, laplacian,
+                                         tile_row, ntiles, Yc, counts, Z,
+                                         work, st, stream));
+    }
+    if (g.chunks > 0) {
+        ProfScope p("k_pull_heavy", stream);
+        GEE_CHECK_CUDA(launch_pull_heavy(g, K, g.weighted, laplacian, Yc,
+                                         counts, Z, hub_part, st, stream));
     }
     if (g.hubs > 0) {
         ProfScope p("k_hub_fixup", stream);
@@ -597,7 +602,8 @@ gee_status gee_graph_create(const int32_t *edges, const float *weights,
 }
 
 gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
-                          int64_t *hub_rows, int64_t *device_bytes)
+                          int64_t *hub_rows, int64_t *hub_arcs,
+                          int64_t *device_bytes)
 {
     if (graph == nullptr)
         return GEE_ERR_INVALID_ARG;
@@ -608,13 +614,15 @@ gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
         *s = c.s;
     if (hub_rows)
         *hub_rows = c.hubs;
+    if (hub_arcs)
+        *hub_arcs = c.hub_arcs;
     if (device_bytes) {
         int64_t b = (c.n + 1) * 8 + (c.nnz_main + 4) * 4 + (c.hub_arcs + 4) * 4;
         if (c.weighted)
             b += (c.nnz_main + c.hub_arcs + 8) * 4;
         if (c.lap_val)
             b += (c.nnz_main + c.hub_arcs + 8) * 4;
-        b += c.hubs * 16 + c.chunks * 12;
+        b += c.hubs * 16 + c.chunks * 12 + (c.n + 1) * 4;
         *device_bytes = b;
     }
     return GEE_OK;

@@ -6,20 +6,23 @@
 //
 //   build_csr      edge list -> symmetric CSR (each edge (u,v,w) gives arcs
 //                  u->v and v->u), rows with more than kHubDegree arcs moved
-//                  to a separate hub CSR cut into chunks of kHubDegree arcs.
+//                  to a separate hub CSR cut into chunks of kHubChunk arcs.
 //   k_partition    splits rows + arcs into tiles of kTileUnits merged units
-//                  (1 per arc, K per row) so every tile moves ~16 KB.
-//   k_pull         per row tile: (A) coalesced arc load + label gather into
-//                  shared memory, (B) each thread walks its share of the
-//                  merged row/arc sequence and adds into a shared-memory
-//                  accumulator of the tile's rows, (C) the tile's Z rows --
-//                  contiguous in Z -- are scaled by 1/n_k and written once.
-//                  Hub chunks accumulate per-class partial sums.
-//   k_hub_fixup    sums each hub's chunk partials in a fixed order and
-//                  writes its Z row.
+//                  (1 per arc, max(K,16) per row) so every tile moves about
+//                  the same number of bytes.
+//   k_pull_light   row tiles of the rows with at most kHubDegree arcs:
+//                  coalesced arc sweep with labels through the read-only
+//                  path (hub labels stay in L1) and shared atomics per
+//                  (row, class), then the tile's Z rows -- contiguous in Z
+//                  -- scaled by 1/n_k and written once.
+//   k_pull_heavy   rows with more arcs, one warp per chunk of kHubChunk arcs;
+//                  single-chunk rows write their Z row, longer rows leave
+//                  per-chunk partial sums.
+//   k_hub_fixup    sums those partials in chunk order and writes the rows.
 //
-// No global atomics touch Z: every Z row is written exactly once (hub rows
-// twice: zeros by their row tile, then the fixup).
+// No global atomics touch Z: every light row is written once; a hub row
+// gets zeros from k_pull_light, then its value from k_pull_heavy or
+// k_hub_fixup, which run after it on the same stream.
 #include "gee_internal.cuh"
 
 namespace gee {
@@ -494,14 +497,29 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 }
 
 // ------------------------------------------------------------ pull
-// Persistent: one CTA per SM, NG independent groups of 256 threads, each
-// synchronised by its own named barrier.  A group repeatedly takes the next
-// work item (row tile or hub chunk) from a global counter.  The CTA first
-// copies the labels of ranks [0, cache_n) into shared memory.
+// Two persistent kernels, one CTA per SM.  Labels are read through the
+// read-only path: with targets stored as degree ranks the most referenced
+// labels are the first bytes of Yc and stay in L1 (measured faster than
+// copying them into shared memory, which also costs the L1 capacity).
+//
+// k_pull_light: rows with at most kHubDegree arcs.  NG independent groups of
+//   128 threads (own named barrier each) take row tiles from a global
+//   counter; per tile: zero the accumulators and load the row starts, sweep
+//   the arcs (16-byte loads, label, binary search for the row, shared
+//   atomic per (row, class)), write the tile's Z rows -- contiguous in Z --
+//   once with 16-byte stores.
+//   Rows kept in the hub CSR have no arcs here and get zeros.
+// k_pull_heavy: rows with more than kHubDegree arcs, cut into chunks of at
+//   most kHubChunk arcs.  One warp per chunk, no block barriers; warps take
+//   contiguous chunk ranges of equal arc counts.  A single-chunk row's Z row
+//   is written directly, overwriting the zeros of k_pull_light (which runs
+//   first); longer rows leave per-chunk partial sums for k_hub_fixup.
 constexpr int kGroupThreads = 128;
 constexpr int kGroups = 8;
-constexpr int kUnroll = 8;  // arcs in flight per thread
-constexpr int kTableCounts = 8;  // counts below this convert by table
+constexpr int kUnroll = 8;        // arcs in flight per thread
+constexpr int kTableCounts = 8;   // counts below this convert by table
+constexpr int kHeavyThreads = 1024;
+constexpr int kHeavyCopies = 1;   // per-warp accumulator copies
 
 struct PullArgs {
     const int64_t *rowptr;
@@ -509,12 +527,15 @@ struct PullArgs {
     const float *val;
     const int32_t *tile_row;
     int64_t ntiles;
-    int64_t nitems;
+    const int32_t *hub_row;
+    const int32_t *hub_chunk0;
     const int32_t *chunk_hub;
     const int64_t *chunk_begin;
     const int64_t *hub_ptr;
     const int32_t *col_h;
     const float *val_h;
+    int64_t chunks;
+    int64_t hub_arcs;
     const uint8_t *Yc;
     const uint32_t *counts;
     float *Z;
@@ -522,11 +543,11 @@ struct PullArgs {
     unsigned long long *work;
     const DevStatus *st;
     int32_t K;
+    uint32_t kmagic;      // floor((2^32-1) / K) + 1: j / K == umulhi(j, kmagic)
     int32_t max_rows;
-    int32_t cache_n;      // labels of ranks [0, cache_n) held in shared memory
-    int32_t cache_bytes;  // cache_n rounded up to 16
-    int32_t group_bytes;
-    int32_t acc_off, lab_off, val_off, slot_off;
+    int32_t area_off;     // start of the per-group / per-warp areas
+    int32_t group_bytes;  // per group (light) or per warp (heavy)
+    int32_t acc_off, slot_off;
 };
 
 __device__ __forceinline__ void group_sync(int g)
@@ -534,11 +555,20 @@ __device__ __forceinline__ void group_sync(int g)
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory");
 }
 
-__device__ __forceinline__ uint32_t label_of(const PullArgs &a,
-                                             const uint8_t *cache, int32_t v,
-                                             uint64_t keep)
+// Label of rank v (read-only path; the most referenced labels -- the front
+// of the rank-ordered array -- stay in L1).
+__device__ __forceinline__ uint32_t label_of(const PullArgs &a, int32_t v)
 {
-    return v < a.cache_n ? (uint32_t)cache[v] : load_label(a.Yc + v, keep);
+    return __ldg(a.Yc + v);
+}
+
+// class of local cell j (the tile's first cell is a multiple of K); the
+// magic multiplier is exact for j < 2^32 / K and does not exist for K = 1
+__device__ __forceinline__ int class_of(const PullArgs &a, int j)
+{
+    if (a.K == 1)
+        return 0;
+    return j - a.K * (int)__umulhi((unsigned)j, a.kmagic);
 }
 
 template <bool WEIGHTED>
@@ -552,82 +582,141 @@ __device__ __forceinline__ float cell_value(uint32_t c, int k,
                                       : count_to_z(c, nk[k]);
 }
 
-// Adds the arcs [0, NA) of a tile or chunk whose first arc is colp[0]
-// (= col + A0, any alignment): 16-byte loads of four arcs for the aligned
-// body, single arcs for the head and tail.  cell_of(i, y) gives the
-// accumulator index of arc i with label y (< 0 to skip it).
-template <bool WEIGHTED, class CellOf>
-__device__ __forceinline__ void sweep_arcs(const PullArgs &a,
-                                           const uint8_t *cache,
-                                           const int32_t *colp,
-                                           const float *valp, int NA, int gt,
-                                           uint32_t *acc, CellOf cell_of)
+// CTA prologue of both pull kernels: n_k and the small-count table (Z
+// values of counts 0..kTableCounts-1).
+template <bool WEIGHTED>
+__device__ __forceinline__ void load_shared(const PullArgs &a, uint32_t *nk,
+                                            float *table)
 {
-    const uint64_t keep = policy_evict_last();
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x)
+        nk[k] = a.counts[k];
+    if (!WEIGHTED)
+        for (int i = threadIdx.x; i < a.K * kTableCounts; i += blockDim.x) {
+            const int k = i / kTableCounts;
+            table[i] = count_to_z((uint32_t)(i - k * kTableCounts),
+                                  a.counts[k]);
+        }
+}
+
+// Accumulator cells of a hub chunk: every arc belongs to the same row.
+struct ChunkCells {
+    int base;
+    __device__ __forceinline__ void at(int) {}
+    __device__ __forceinline__ int cell(int, uint32_t y) const
+    {
+        return base + (int)y;
+    }
+};
+
+// Accumulator cells of a row tile: rp[r] is the first arc of local row r
+// (rp[NR] = NA).  at(i) finds the row of arc i by binary search; cell()
+// then advances row by row for the following arcs.
+struct TileCells {
+    const int32_t *rp;
+    int NR, K, off;
+    int row, next;
+    __device__ __forceinline__ void at(int i)
+    {
+        int lo = 0, hi = NR - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rp[mid] <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        row = lo;
+        next = rp[lo + 1];
+    }
+    __device__ __forceinline__ int cell(int i, uint32_t y)
+    {
+        while (i >= next) {
+            ++row;
+            next = rp[row + 1];
+        }
+        return off + row * K + (int)y;
+    }
+};
+
+// Adds the arcs [0, NA) that start at colp[0] (any alignment) with NT
+// threads, t = this thread: 16-byte loads of four arcs for the aligned body
+// (full rounds of kUnroll arcs per thread unguarded, then a guarded rest),
+// single arcs for the head and tail.  cells maps (arc, label) to an
+// accumulator index; arcs whose label is unknown go to this thread's own
+// sink cell (no branch, no shared-address contention).
+template <bool WEIGHTED, int NT, class Cells>
+__device__ __forceinline__ void sweep_arcs(const PullArgs &a,
+                                           const int32_t *colp,
+                                           const float *valp, int NA, int t,
+                                           uint32_t *acc, int sink,
+                                           Cells &cells)
+{
     float *accf = reinterpret_cast<float *>(acc);
+    auto add = [&](int i, uint32_t y, float w) {
+        const int c = y != kNoLabel ? cells.cell(i, y) : sink;
+        if (WEIGHTED)
+            atomicAdd(accf + c, w);
+        else
+            atomicAdd(acc + c, 1u);
+    };
     const int head =
         min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
-    auto one = [&](int i, int32_t v, float w) {
-        const uint32_t y = label_of(a, cache, v, keep);
-        if (y != kNoLabel) {
-            const int c = cell_of(i, y);
-            if (WEIGHTED)
-                atomicAdd(accf + c, w);
-            else
-                atomicAdd(acc + c, 1u);
-        }
-    };
-    if (gt < head)
-        one(gt, colp[gt], WEIGHTED ? valp[gt] : 0.0f);
+    if (t < head) {
+        cells.at(t);
+        add(t, label_of(a, colp[t]), WEIGHTED ? valp[t] : 0.0f);
+    }
     const int nq = (NA - head) >> 2;
     const int4 *col4 = reinterpret_cast<const int4 *>(colp + head);
     const float4 *val4 = reinterpret_cast<const float4 *>(valp + head);
-    constexpr int kQ = kUnroll / 4;  // quads in flight per thread
-    for (int q0 = gt; q0 < nq; q0 += kQ * kGroupThreads) {
+    constexpr int kQ = kUnroll / 4;  // quads per thread per round
+    auto round = [&](int q0, bool guard) {
         int4 c[kQ];
         float4 w[kQ];
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
-            const int q = q0 + u * kGroupThreads;
-            c[u] = q < nq ? __ldcs(col4 + q) : make_int4(0, 0, 0, 0);
+            const int q = q0 + u * NT;
+            const bool ok = !guard || q < nq;
+            c[u] = ok ? __ldcs(col4 + q) : make_int4(0, 0, 0, 0);
             if (WEIGHTED)
-                w[u] = q < nq ? __ldcs(val4 + q) : make_float4(0, 0, 0, 0);
+                w[u] = ok ? __ldcs(val4 + q) : make_float4(0, 0, 0, 0);
         }
         uint32_t y[kUnroll];
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
-            const bool ok = q0 + u * kGroupThreads < nq;
-            y[4 * u + 0] = ok ? label_of(a, cache, c[u].x, keep) : kNoLabel;
-            y[4 * u + 1] = ok ? label_of(a, cache, c[u].y, keep) : kNoLabel;
-            y[4 * u + 2] = ok ? label_of(a, cache, c[u].z, keep) : kNoLabel;
-            y[4 * u + 3] = ok ? label_of(a, cache, c[u].w, keep) : kNoLabel;
+            y[4 * u + 0] = label_of(a, c[u].x);
+            y[4 * u + 1] = label_of(a, c[u].y);
+            y[4 * u + 2] = label_of(a, c[u].z);
+            y[4 * u + 3] = label_of(a, c[u].w);
         }
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
-            const int i0 = head + 4 * (q0 + u * kGroupThreads);
-            const float ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint32_t yy = y[4 * u + e];
-                if (yy != kNoLabel) {
-                    const int cc = cell_of(i0 + e, yy);
-                    if (WEIGHTED)
-                        atomicAdd(accf + cc, ws[e]);
-                    else
-                        atomicAdd(acc + cc, 1u);
-                }
+            const int q = q0 + u * NT;
+            if (!guard || q < nq) {
+                const int i0 = head + 4 * q;
+                cells.at(i0);
+                add(i0 + 0, y[4 * u + 0], WEIGHTED ? w[u].x : 0.0f);
+                add(i0 + 1, y[4 * u + 1], WEIGHTED ? w[u].y : 0.0f);
+                add(i0 + 2, y[4 * u + 2], WEIGHTED ? w[u].z : 0.0f);
+                add(i0 + 3, y[4 * u + 3], WEIGHTED ? w[u].w : 0.0f);
             }
         }
-    }
+    };
+    const int full = nq / (kQ * NT) * (kQ * NT);
+    for (int q0 = t; q0 < full; q0 += kQ * NT)
+        round(q0, false);
+    if (full + t < nq)
+        round(full + t, true);
     const int tail0 = head + 4 * nq;
-    if (gt < NA - tail0)
-        one(tail0 + gt, colp[tail0 + gt], WEIGHTED ? valp[tail0 + gt] : 0.0f);
+    if (t < NA - tail0) {
+        cells.at(tail0 + t);
+        add(tail0 + t, label_of(a, colp[tail0 + t]),
+            WEIGHTED ? valp[tail0 + t] : 0.0f);
+    }
 }
 
 template <bool WEIGHTED>
 __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                                          unsigned char *gs,
-                                         const uint8_t *cache,
                                          const uint32_t *nk,
                                          const float *table, int64_t t)
 {
@@ -635,175 +724,171 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     const int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
     if (r0 == r1)
         return;
-    const int NR = r1 - r0;  // <= 128, so a local row fits in a byte
-    uint8_t *row_of = gs;    // local row of every arc of the tile
+    const int NR = r1 - r0;
+    int32_t *rp = reinterpret_cast<int32_t *>(gs);  // row starts, tile-relative
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
 
     const int64_t g0 = (int64_t)r0 * K;  // first Z cell of the tile
     const int off = (int)(g0 & 3);       // acc[off + j] holds cell g0 + j
     const int cells = NR * K;
-    const int lane = gt & 31, warp = gt >> 5;
-    constexpr int kWarps = kGroupThreads / 32;
 
-    // setup: zero the accumulators; warp w labels the arcs of rows w, w+4,
-    // ... (lane j holds the bounds of row w + 4j)
+    // setup: zero the accumulators, load the tile's row starts
     {
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
         for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
             acc4[c] = make_uint4(0u, 0u, 0u, 0u);
     }
     const int64_t A0 = a.rowptr[r0];
-    const int NA = (int)(a.rowptr[r1] - A0);
-    {
-        const int myrow = warp + kWarps * lane;
-        int b = 0, e = 0;
-        if (myrow < NR) {
-            b = (int)(a.rowptr[r0 + myrow] - A0);
-            e = (int)(a.rowptr[r0 + myrow + 1] - A0);
-        }
-        for (int j = 0; warp + kWarps * j < NR; ++j) {
-            const int bj = __shfl_sync(0xffffffffu, b, j);
-            const int ej = __shfl_sync(0xffffffffu, e, j);
-            const uint8_t row = (uint8_t)(warp + kWarps * j);
-            for (int i = bj + lane; i < ej; i += 32)
-                row_of[i] = row;
-        }
+    for (int i = gt; i <= NR; i += kGroupThreads)
+        rp[i] = (int32_t)(a.rowptr[r0 + i] - A0);
+    group_sync(g);
+    const int NA = rp[NR];
+
+    // sweep: the row of arc i is the last row starting at or before i
+    if (NA > 0) {
+        TileCells cells{rp, NR, K, off, 0, 0};
+        sweep_arcs<WEIGHTED, kGroupThreads>(
+            a, a.col + A0, WEIGHTED ? a.val + A0 : nullptr, NA, gt, acc,
+            a.max_rows * K + 8 + (gt & 31), cells);
     }
     group_sync(g);
 
-    // (A) one coalesced sweep over the tile's arcs: label from the shared
-    //     cache or through L2, then add into the arc's row accumulator
-    sweep_arcs<WEIGHTED>(a, cache, a.col + A0,
-                         WEIGHTED ? a.val + A0 : nullptr, NA, gt, acc,
-                         [&](int i, uint32_t y) {
-                             return off + (int)row_of[i] * K + (int)y;
-                         });
-    group_sync(g);
-
-    // (C) the tile's rows are contiguous in Z: scale once and stream out,
-    //     16-byte stores between an unaligned head and tail (g0 is a
-    //     multiple of K, so cell j has class j mod K)
+    // the tile's rows are contiguous in Z: scale once and stream out with
+    // 16-byte stores between an unaligned head and tail; all-zero quads
+    // (most of them: isolated nodes, sparse rows) skip the conversion
     float *z = a.Z + g0;
     const int head = min((4 - off) & 3, cells);
     if (gt < head)
-        __stcs(z + gt, cell_value<WEIGHTED>(acc[off + gt], gt % K, nk, table));
+        __stcs(z + gt, cell_value<WEIGHTED>(acc[off + gt], class_of(a, gt), nk,
+                                            table));
     const int nq = (cells - head) >> 2;
-    if (gt < nq) {
-        int k = (head + 4 * gt) % K;
-        const int kstep = (4 * kGroupThreads) % K;
-        for (int q = gt; q < nq; q += kGroupThreads) {
-            const int j0 = head + 4 * q;
-            const uint4 c4 = *reinterpret_cast<const uint4 *>(acc + off + j0);
-            float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
-                const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
-                float o[4];
-                int kk = k;
+    for (int q = gt; q < nq; q += kGroupThreads) {
+        const int j0 = head + 4 * q;
+        const uint4 c4 = *reinterpret_cast<const uint4 *>(acc + off + j0);
+        float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
+            int k = class_of(a, j0);
+            const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+            float o[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    o[e] = cell_value<WEIGHTED>(cs[e], kk, nk, table);
-                    if (++kk == K)
-                        kk = 0;
-                }
-                o4 = make_float4(o[0], o[1], o[2], o[3]);
+            for (int e = 0; e < 4; ++e) {
+                o[e] = cell_value<WEIGHTED>(cs[e], k, nk, table);
+                if (++k == K)
+                    k = 0;
             }
-            __stcs(reinterpret_cast<float4 *>(z + j0), o4);
-            k += kstep;
-            if (k >= K)
-                k -= K;
+            o4 = make_float4(o[0], o[1], o[2], o[3]);
         }
+        __stcs(reinterpret_cast<float4 *>(z + j0), o4);
     }
     const int tail0 = head + 4 * nq;
     if (gt < cells - tail0) {
         const int j = tail0 + gt;
-        __stcs(z + j, cell_value<WEIGHTED>(acc[off + j], j % K, nk, table));
+        __stcs(z + j, cell_value<WEIGHTED>(acc[off + j], class_of(a, j), nk,
+                                           table));
     }
 }
 
 template <bool WEIGHTED>
-__device__ __forceinline__ void hub_chunk(const PullArgs &a, int g, int gt,
-                                          unsigned char *gs,
-                                          const uint8_t *cache, int64_t c)
-{
-    const int32_t K = a.K;
-    uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);  // [8][K]
-    float *accf = reinterpret_cast<float *>(acc);
-    constexpr int kWarps = kGroupThreads / 32;
-    for (int i = gt; i < kWarps * K; i += kGroupThreads)
-        acc[i] = 0u;
-    group_sync(g);
-    const int32_t h = a.chunk_hub[c];
-    const int64_t b = a.chunk_begin[c];
-    const int64_t hend = a.hub_ptr[h + 1];
-    const int64_t e = (b + kHubChunk < hend) ? b + kHubChunk : hend;
-    const int n = (int)(e - b);
-    const int warp_base = (gt >> 5) * K;
-    sweep_arcs<WEIGHTED>(a, cache, a.col_h + b,
-                         WEIGHTED ? a.val_h + b : nullptr, n, gt, acc,
-                         [&](int, uint32_t y) { return warp_base + (int)y; });
-    group_sync(g);
-    for (int k = gt; k < K; k += kGroupThreads) {
-        if (WEIGHTED) {
-            float s = 0.0f;
-            for (int w = 0; w < kWarps; ++w)
-                s += accf[w * K + k];
-            reinterpret_cast<float *>(a.hub_part)[c * K + k] = s;
-        } else {
-            uint32_t s = 0;
-            for (int w = 0; w < kWarps; ++w)
-                s += acc[w * K + k];
-            a.hub_part[c * K + k] = s;
-        }
-    }
-}
-
-template <bool WEIGHTED, int NG>
-__global__ void __launch_bounds__(NG *kGroupThreads, 1) k_pull(PullArgs a)
+__global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
+    k_pull_light(PullArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     if (failed(a.st))
         return;
-    const int32_t K = a.K;
-    uint8_t *cache = sm;
-    uint32_t *nk = reinterpret_cast<uint32_t *>(sm + a.cache_bytes);
+    uint32_t *nk = reinterpret_cast<uint32_t *>(sm);
     float *table = reinterpret_cast<float *>(nk + 256);
-    unsigned char *groups =
-        reinterpret_cast<unsigned char *>(table + 256 * kTableCounts);
-    // the CTA's copy of the most-referenced labels (16-byte copies)
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.Yc);
-        uint4 *dst = reinterpret_cast<uint4 *>(cache);
-        for (int i = threadIdx.x; i < a.cache_bytes / 16; i += blockDim.x)
-            dst[i] = src[i];
-    }
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        nk[k] = a.counts[k];
-    if (!WEIGHTED)
-        for (int i = threadIdx.x; i < K * kTableCounts; i += blockDim.x) {
-            const int k = i / kTableCounts;
-            table[i] = count_to_z((uint32_t)(i - k * kTableCounts),
-                                  a.counts[k]);
-        }
+    load_shared<WEIGHTED>(a, nk, table);
     __syncthreads();
     const int g = threadIdx.x / kGroupThreads;
     const int gt = threadIdx.x - g * kGroupThreads;
-    unsigned char *gs = groups + (size_t)g * a.group_bytes;
+    unsigned char *gs = sm + a.area_off + (size_t)g * a.group_bytes;
     long long *slot = reinterpret_cast<long long *>(gs + a.slot_off);
     for (int it = 0;; ++it) {
         if (gt == 0)
             slot[it & 1] = (long long)atomicAdd(a.work, 1ull);
         group_sync(g);
         const int64_t item = slot[it & 1];
-        if (item >= a.nitems)
+        if (item >= a.ntiles)
             break;
-        if (item < a.ntiles)
-            row_tile<WEIGHTED>(a, g, gt, gs, cache, nk, table, item);
-        else
-            hub_chunk<WEIGHTED>(a, g, gt, gs, cache, item - a.ntiles);
+        row_tile<WEIGHTED>(a, g, gt, gs, nk, table, item);
     }
 }
 
-// One warp per hub row: chunk partials summed in chunk order, then scaled.
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    if (failed(a.st))
+        return;
+    uint32_t *nk = reinterpret_cast<uint32_t *>(sm);
+    float *table = reinterpret_cast<float *>(nk + 256);
+    load_shared<WEIGHTED>(a, nk, table);
+    __syncthreads();
+    const int32_t K = a.K;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *acc = reinterpret_cast<uint32_t *>(sm + a.area_off +
+                                                 (size_t)wib * a.group_bytes);
+    float *accf = reinterpret_cast<float *>(acc);
+    // this warp's chunks: those whose first arc lies in its equal share of
+    // the hub arcs (chunk_begin is increasing)
+    const int64_t nw = (int64_t)gridDim.x * (kHeavyThreads / 32);
+    const int64_t w = (int64_t)blockIdx.x * (kHeavyThreads / 32) + wib;
+    auto first_chunk_at = [&](int64_t arc) {
+        int64_t lo = 0, hi = a.chunks;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.chunk_begin[mid] < arc)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        return lo;
+    };
+    const int64_t c_lo = first_chunk_at(a.hub_arcs * w / nw);
+    const int64_t c_hi = first_chunk_at(a.hub_arcs * (w + 1) / nw);
+    const int copy = (lane & (kHeavyCopies - 1)) * K;
+    for (int64_t c = c_lo; c < c_hi; ++c) {
+        for (int i = lane; i < kHeavyCopies * K; i += 32)
+            acc[i] = 0u;
+        __syncwarp();
+        const int32_t h = a.chunk_hub[c];
+        const int64_t b = a.chunk_begin[c];
+        const int64_t hend = a.hub_ptr[h + 1];
+        const int n = (int)((b + kHubChunk < hend ? b + kHubChunk : hend) - b);
+        ChunkCells cells{copy};
+        sweep_arcs<WEIGHTED, 32>(a, a.col_h + b,
+                                 WEIGHTED ? a.val_h + b : nullptr, n, lane,
+                                 acc, kHeavyCopies * K + lane, cells);
+        __syncwarp();
+        const bool whole = a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
+        float *zrow = a.Z + (int64_t)a.hub_row[h] * K;
+        for (int k = lane; k < K; k += 32) {
+            uint32_t bits;
+            if (WEIGHTED) {
+                float s = 0.0f;
+#pragma unroll
+                for (int r = 0; r < kHeavyCopies; ++r)
+                    s += accf[r * K + k];
+                bits = __float_as_uint(s);
+            } else {
+                uint32_t s = 0;
+#pragma unroll
+                for (int r = 0; r < kHeavyCopies; ++r)
+                    s += acc[r * K + k];
+                bits = s;
+            }
+            if (whole)
+                zrow[k] = cell_value<WEIGHTED>(bits, k, nk, table);
+            else
+                a.hub_part[c * K + k] = bits;
+        }
+        __syncwarp();
+    }
+}
+
+// One warp per hub row cut into several chunks: partials summed in chunk
+// order, then scaled.  Single-chunk rows were written by k_pull_heavy.
 template <bool WEIGHTED>
 __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
                             const int32_t *__restrict__ hub_chunk0,
@@ -818,6 +903,8 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t h = warp; h < hubs; h += nwarps) {
         const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
+        if (c1 - c0 < 2)
+            continue;
         float *zrow = Z + (int64_t)hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
             if (WEIGHTED) {
@@ -837,45 +924,23 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
 
 inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-struct PullLayout {
-    int groups;
-    size_t total;
-};
-
-// Shared-memory plan: [label cache][n_k (256)][table 256 x 8][groups...].
-PullLayout plan_pull(const Csr &g, int32_t K, bool weighted, PullArgs &a)
+int optin_smem()
 {
-    const int C = row_cost(K);
-    a.max_rows = (kTileUnits + C - 1) / C;
-    const size_t rowof = align16(kMaxTileArcs);
-    // +8 cells: the offset (< 4) and the 16-byte rounding of the zeroing
-    const size_t accb = align16((size_t)(a.max_rows * K + 8) * 4);
-    a.acc_off = (int32_t)rowof;
-    a.lab_off = 0;
-    a.val_off = 0;
-    a.slot_off = (int32_t)(rowof + accb);
-    a.group_bytes = (int32_t)(a.slot_off + 16);
-    const int groups = kGroups;
-    const size_t fixed = 256 * 4 + 256 * kTableCounts * 4 +
-                         (size_t)groups * a.group_bytes;
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                dev) != cudaSuccess)
         optin = 227 * 1024;
-    int64_t room = (int64_t)optin - (int64_t)fixed - 256;
-    room = room < 0 ? 0 : (room & ~int64_t(15));
-    int64_t cache = g.n < room ? g.n : room;
-    a.cache_n = (int32_t)cache;
-    a.cache_bytes = (int32_t)((cache + 15) & ~int64_t(15));
-    if (a.cache_bytes > room) {  // rounding up must not overflow the plan
-        a.cache_bytes = (int32_t)room;
-        a.cache_n = (int32_t)room;
-    }
-    PullLayout L;
-    L.groups = groups;
-    L.total = (size_t)a.cache_bytes + fixed;
-    return L;
+    return optin;
+}
+
+// Shared memory: [n_k (256)][table 256 x 8][per-group / per-warp areas].
+// Returns the bytes to launch with.
+size_t plan_shared(size_t area_bytes, PullArgs &a)
+{
+    const size_t fixed = 256 * 4 + 256 * kTableCounts * 4;
+    a.area_off = (int32_t)fixed;
+    return fixed + area_bytes;
 }
 
 }  // namespace
@@ -1051,37 +1116,39 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
     return cudaGetLastError();
 }
 
-template <bool W, int NG>
-static cudaError_t pull_launch_t(const PullArgs &a, size_t smem,
-                                 cudaStream_t stream)
+template <class Kern>
+static cudaError_t launch_persistent(Kern kernel, int threads, size_t smem,
+                                     const PullArgs &a, cudaStream_t stream)
 {
     cudaError_t e = cudaFuncSetAttribute(
-        k_pull<W, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_pull<W, NG><<<sm_count(), NG * kGroupThreads, smem, stream>>>(a);
+    kernel<<<sm_count(), threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pull(const Csr &g, int32_t K, bool weighted,
-                        bool laplacian, const int32_t *tile_row,
-                        int64_t ntiles, const uint8_t *Yc,
-                        const uint32_t *counts, float *Z, void *hub_part,
-                        unsigned long long *work, const DevStatus *st,
-                        cudaStream_t stream)
+static PullArgs pull_args(const Csr &g, int32_t K, bool laplacian,
+                          const int32_t *tile_row, int64_t ntiles,
+                          const uint8_t *Yc, const uint32_t *counts, float *Z,
+                          void *hub_part, unsigned long long *work,
+                          const DevStatus *st)
 {
-    PullArgs a;
+    PullArgs a = {};
     a.rowptr = g.rowptr;
     a.col = g.col;
     a.val = laplacian ? g.lap_val : g.val;
     a.tile_row = tile_row;
     a.ntiles = ntiles;
-    a.nitems = ntiles + g.chunks;
+    a.hub_row = g.hub_row;
+    a.hub_chunk0 = g.hub_chunk0;
     a.chunk_hub = g.chunk_hub;
     a.chunk_begin = g.chunk_begin;
     a.hub_ptr = g.hub_ptr;
     a.col_h = g.col_h;
     a.val_h = laplacian ? g.lap_val_h : g.val_h;
+    a.chunks = g.chunks;
+    a.hub_arcs = g.hub_arcs;
     a.Yc = Yc;
     a.counts = counts;
     a.Z = Z;
@@ -1089,15 +1156,60 @@ cudaError_t launch_pull(const Csr &g, int32_t K, bool weighted,
     a.work = work;
     a.st = st;
     a.K = K;
-    const bool wpath = weighted || laplacian;
-    const PullLayout L = plan_pull(g, K, wpath, a);
-    if (a.nitems == 0)
+    a.kmagic = K > 1 ? (uint32_t)(0xFFFFFFFFull / (uint32_t)K + 1ull) : 0u;
+    return a;
+}
+
+cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
+                              bool laplacian, const int32_t *tile_row,
+                              int64_t ntiles, const uint8_t *Yc,
+                              const uint32_t *counts, float *Z,
+                              unsigned long long *work, const DevStatus *st,
+                              cudaStream_t stream)
+{
+    if (ntiles == 0)
         return cudaSuccess;
+    PullArgs a = pull_args(g, K, laplacian, tile_row, ntiles, Yc, counts, Z,
+                           nullptr, work, st);
+    const int C = row_cost(K);
+    a.max_rows = (kTileUnits + C - 1) / C;
+    const size_t rpb = align16((size_t)(a.max_rows + 2) * 4);
+    // +8 cells: the offset (< 4) and the 16-byte rounding of the zeroing;
+    // then 32 sink cells (one per lane) for arcs of unknown label
+    const size_t accb = align16((size_t)(a.max_rows * K + 8 + 32) * 4);
+    a.acc_off = (int32_t)rpb;
+    a.slot_off = (int32_t)(rpb + accb);
+    a.group_bytes = (int32_t)(a.slot_off + 16);
+    const size_t smem = plan_shared((size_t)kGroups * a.group_bytes, a);
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess)
         return e;
-    return wpath ? pull_launch_t<true, kGroups>(a, L.total, stream)
-                 : pull_launch_t<false, kGroups>(a, L.total, stream);
+    return (weighted || laplacian)
+               ? launch_persistent(k_pull_light<true>, kGroups * kGroupThreads,
+                                   smem, a, stream)
+               : launch_persistent(k_pull_light<false>, kGroups * kGroupThreads,
+                                   smem, a, stream);
+}
+
+cudaError_t launch_pull_heavy(const Csr &g, int32_t K, bool weighted,
+                              bool laplacian, const uint8_t *Yc,
+                              const uint32_t *counts, float *Z,
+                              void *hub_part, const DevStatus *st,
+                              cudaStream_t stream)
+{
+    if (g.chunks == 0)
+        return cudaSuccess;
+    PullArgs a = pull_args(g, K, laplacian, nullptr, 0, Yc, counts, Z,
+                           hub_part, nullptr, st);
+    // kHeavyCopies accumulators of K cells, then 32 sink cells
+    a.group_bytes = (int32_t)align16((size_t)(kHeavyCopies * K + 32) * 4);
+    const size_t smem =
+        plan_shared((size_t)(kHeavyThreads / 32) * a.group_bytes, a);
+    return (weighted || laplacian)
+               ? launch_persistent(k_pull_heavy<true>, kHeavyThreads, smem, a,
+                                   stream)
+               : launch_persistent(k_pull_heavy<false>, kHeavyThreads, smem, a,
+                                   stream);
 }
 
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,

@@ -21,9 +21,10 @@ constexpr int kMaxClasses = GEE_MAX_CLASSES;
 // arc plus max(K, 16) units per row (the row's Z write), so that every tile
 // moves about the same number of bytes.  Rows with more than kHubDegree arcs
 // are processed apart, in chunks of kHubChunk arcs.
-constexpr int kTileUnits = 2048;
+constexpr int kTileUnits = 4096;
 constexpr int kHubDegree = GEE_HUB_DEGREE;
 constexpr int kHubChunk = 2048;
+
 constexpr int kMaxTileArcs = kTileUnits + kHubDegree;
 
 // First error a kernel saw.  `index` is the smallest offending element.
@@ -191,16 +192,23 @@ int64_t pull_tiles(const Csr &g, int32_t K);
 cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
                              int64_t ntiles, cudaStream_t stream);
 
-// S4 + S5 (CSR form): writes every row of Z exactly once; hub rows get
-// zeros here and their values from launch_hub_fixup, which must follow.
-// Yc is in rank order.  hub_part: scratch [chunks * K] of 4-byte per-chunk
-// partial sums; work: one 8-byte scratch counter.
-cudaError_t launch_pull(const Csr &g, int32_t K, bool weighted,
-                        bool laplacian, const int32_t *tile_row,
-                        int64_t ntiles, const uint8_t *Yc,
-                        const uint32_t *counts, float *Z, void *hub_part,
-                        unsigned long long *work, const DevStatus *st,
-                        cudaStream_t stream);
+// S4 + S5 (CSR form), three launches in this order on one stream:
+// light rows (every Z row of the tile range; hub rows get zeros), hub-row
+// chunks (single-chunk hub rows written directly) and the fixup of hub rows
+// with several chunks.  Yc is in rank order.  hub_part: scratch
+// [chunks * K] of 4-byte per-chunk partial sums; work: one 8-byte scratch
+// counter.
+cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
+                              bool laplacian, const int32_t *tile_row,
+                              int64_t ntiles, const uint8_t *Yc,
+                              const uint32_t *counts, float *Z,
+                              unsigned long long *work, const DevStatus *st,
+                              cudaStream_t stream);
+cudaError_t launch_pull_heavy(const Csr &g, int32_t K, bool weighted,
+                              bool laplacian, const uint8_t *Yc,
+                              const uint32_t *counts, float *Z,
+                              void *hub_part, const DevStatus *st,
+                              cudaStream_t stream);
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
                              const void *hub_part, const DevStatus *st,

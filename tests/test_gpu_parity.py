@@ -106,6 +106,9 @@ RANDOM_CASES = [
     (3001, 40000, 255, 0.0), # K at its maximum
     (4000, 30000, 1, 0.0),   # K = 1
     (500, 20000, 7, 1.0),    # nothing labelled
+    (200, 30000, 7, 0.1),    # every row above the hub threshold, one chunk
+    (300, 40000, 255, 0.0),  # hub rows with K at its maximum
+    (64, 200000, 3, 0.0),    # hub rows of several chunks, tiny K
 ]
 
 
