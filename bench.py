@@ -75,10 +75,12 @@ def measured_peaks():
 
 
 def source_digest():
+    """Digest of the edge-pass kernel sources (the ncu traffic figure is only
+    reported while it matches)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2402_04403_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
+    for name in ("gee_csr.cu", "gee_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2402_04403_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -353,7 +355,8 @@ def run_ours(args, w, world, rank, local):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "traffic": ncu_traffic("k_pull", args.workload),
+                     "traffic": ncu_traffic("k_pull", args.workload)
+                     if not args.scale_shift else None,
                      "algorithmic_bytes_per_launch": pull_bytes(w),
                      "avg_launch_ms": pass_ms,
                      "step_algorithmic_bytes": algorithmic_bytes(w),
