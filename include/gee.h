@@ -61,6 +61,8 @@ extern "C" {
 typedef struct CUstream_st *gee_stream_t;
 
 #define GEE_MAX_CLASSES 255
+/* Z columns of one multi-label pass (label vectors x classes). */
+#define GEE_MAX_COLUMNS 1024
 
 typedef enum gee_status {
     GEE_OK = 0,
@@ -150,6 +152,21 @@ GEE_API gee_status gee_graph_create(const int32_t *edges, const float *weights,
 GEE_API gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
                            int32_t laplacian, float *Z,
                            const gee_options *opts, gee_stream_t stream);
+
+/*
+ * L label vectors on one resident graph in a single pass: a W widened to
+ * L*K columns, so every arc is read and its target's L labels gathered once
+ * for all L embeddings (used for repeated re-labelings, e.g. unsupervised
+ * GEE iterations).  Y: device int32 [L][n], vector l at Y + l*n.  Z: device
+ * float [n][L*K] row-major, Z[u][l*K + k] = the embedding of node u for
+ * label vector l.  Each vector has its own class sizes.  L >= 1, L*K <=
+ * GEE_MAX_COLUMNS.  Same results as L separate gee_embed_graph calls.
+ */
+GEE_API gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
+                                         int32_t L, int32_t K,
+                                         int32_t laplacian, float *Z,
+                                         const gee_options *opts,
+                                         gee_stream_t stream);
 
 /* Same with host Y_h and Z_h (e.g. pinned buffers). */
 GEE_API gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,

@@ -233,6 +233,24 @@ class Graph:
         check(rc, "gee_embed_graph")
         return out
 
+    def embed_multi(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+        """L label vectors (Y: int32 (L, n)) in one pass; returns Z of shape
+        (n, L*K) with columns [l*K, (l+1)*K) for vector l
+        (gee_embed_graph_multi)."""
+        torch = _torch()
+        if Y.dim() != 2 or Y.shape[1] != self.n:
+            raise ValueError("Y must have shape (L, n)")
+        L = Y.shape[0]
+        if out is None:
+            out = torch.empty((self.n, L * K), dtype=torch.float32, device=Y.device)
+        o = options()
+        rc = lib().gee_embed_graph_multi(
+            self.handle, _dev_ptr(Y, torch.int32, "Y"), int(L), int(K),
+            int(bool(laplacian)), _dev_ptr(out, torch.float32, "out", (self.n, L * K)),
+            ctypes.byref(o), _stream_handle(stream))
+        check(rc, "gee_embed_graph_multi")
+        return out
+
     def embed_host(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
         import numpy as np
         Yv = _host_buf(Y)

@@ -25,6 +25,7 @@ STATUS = {v: k for k, v in STATUS_NAMES.items()}
 STRATEGIES = {"auto": 0, "atomic": 1, "private": 2, "segmented": 3}
 STRATEGY_NAMES = {v: k for k, v in STRATEGIES.items()}
 MAX_CLASSES = 255
+MAX_COLUMNS = 1024
 NOALLOC_MAX_NODES = (16 << 20) - 2048
 HUB_DEGREE = 128
 
@@ -75,6 +76,7 @@ SIGNATURES = {
     "gee_graph_create": (ctypes.c_int, [_P, _P, _I64, _I64, _P, ctypes.POINTER(_P)]),
     "gee_embed_graph": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _OPT, _P]),
     "gee_embed_graph_host": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _OPT, _P]),
+    "gee_embed_graph_multi": (ctypes.c_int, [_P, _P, _I32, _I32, _I32, _P, _OPT, _P]),
     "gee_graph_info": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 5),
     "gee_graph_destroy": (None, [_P]),
     "gee_pick_strategy": (ctypes.c_int, [_I64, _I64, _I32, _OPT]),

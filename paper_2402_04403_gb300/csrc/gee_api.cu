@@ -155,16 +155,22 @@ gee_status check_common(int64_t s, int64_t n, int32_t K, int32_t threads)
 
 // Scratch of one call: status word, n_k, compact labels (n + 16 bytes).
 gee_status step_begin(Workspace &ws, int64_t n, int32_t K, DevStatus **st,
-                      uint32_t **counts, uint8_t **Yc, cudaStream_t stream)
+                      uint32_t **counts, uint8_t **Yc, cudaStream_t stream,
+                      int32_t L = 1)
 {
     GEE_CHECK_CUDA(ws.alloc((void **)st, sizeof(DevStatus)));
-    GEE_CHECK_CUDA(ws.alloc((void **)counts, sizeof(uint32_t) * kMaxClasses));
-    GEE_CHECK_CUDA(ws.alloc((void **)Yc, (size_t)n + 16));
+    GEE_CHECK_CUDA(ws.alloc((void **)counts,
+                            sizeof(uint32_t) * (L * K > kMaxClasses
+                                                    ? L * K
+                                                    : kMaxClasses)));
+    GEE_CHECK_CUDA(ws.alloc((void **)Yc,
+                            (size_t)n * (L > 1 ? label_stride(L) : 1) + 16));
     {
         ProfScope p("k_status_init", stream);
         GEE_CHECK_CUDA(launch_status_init(*st, stream));
     }
-    GEE_CHECK_CUDA(cudaMemsetAsync(*counts, 0, sizeof(uint32_t) * K, stream));
+    GEE_CHECK_CUDA(
+        cudaMemsetAsync(*counts, 0, sizeof(uint32_t) * K * L, stream));
     return GEE_OK;
 }
 
@@ -191,38 +197,41 @@ gee_status labels_step(Workspace &ws, const int32_t *Y, int64_t n, int32_t K,
     return labels_launch(Y, n, K, rank, *Yc, *counts, *st, stream);
 }
 
-// S4 + S5 over a CSR (resident or built for this call).
+// S4 + S5 over a CSR (resident or built for this call), for L label
+// vectors of K classes (Z rows of L*K columns).
 gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                      const uint8_t *Yc, const uint32_t *counts, float *Z,
-                     const DevStatus *st, cudaStream_t stream)
+                     const DevStatus *st, cudaStream_t stream, int32_t L = 1)
 {
-    const int64_t ntiles = pull_tiles(g, K);
+    const int32_t cols = L * K;
+    const int64_t ntiles = pull_tiles(g, cols);
     int32_t *tile_row = nullptr;
     void *hub_part = nullptr;
     unsigned long long *work = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&work, sizeof(unsigned long long)));
     GEE_CHECK_CUDA(ws.alloc((void **)&tile_row,
                             sizeof(int32_t) * (ntiles + 1)));
-    GEE_CHECK_CUDA(ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * K + 1)));
+    GEE_CHECK_CUDA(
+        ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
     {
         ProfScope p("k_partition", stream);
-        GEE_CHECK_CUDA(launch_partition(g, K, tile_row, ntiles, stream));
+        GEE_CHECK_CUDA(launch_partition(g, cols, tile_row, ntiles, stream));
     }
     {
         ProfScope p("k_pull_light", stream);
-        GEE_CHECK_CUDA(launch_pull_light(g, K, g.weighted, laplacian,
+        GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
                                          tile_row, ntiles, Yc, counts, Z,
                                          work, st, stream));
     }
     if (g.chunks > 0) {
         ProfScope p("k_pull_heavy", stream);
-        GEE_CHECK_CUDA(launch_pull_heavy(g, K, g.weighted, laplacian, Yc,
+        GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
                                          counts, Z, hub_part, st, stream));
     }
     if (g.hubs > 0) {
         ProfScope p("k_hub_fixup", stream);
-        GEE_CHECK_CUDA(launch_hub_fixup(g, K, g.weighted, laplacian, counts, Z,
-                                        hub_part, st, stream));
+        GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian, counts,
+                                        Z, hub_part, st, stream));
     }
     return GEE_OK;
 }
@@ -362,7 +371,7 @@ gee_status ensure_laplacian(gee_graph *g, cudaStream_t stream)
 
 gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
                            int32_t K, int32_t laplacian, float *Z,
-                           cudaStream_t stream)
+                           cudaStream_t stream, int32_t L = 1)
 {
     if (laplacian) {
         gee_status rc = ensure_laplacian(graph, stream);
@@ -372,13 +381,23 @@ gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
     DevStatus *st;
     uint32_t *counts;
     uint8_t *Yc;
-    gee_status rc =
-        labels_step(ws, Y, graph->csr.n, K, graph->csr.rank, &st, &counts, &Yc,
-                    stream);
+    gee_status rc;
+    if (L == 1) {
+        rc = labels_step(ws, Y, graph->csr.n, K, graph->csr.rank, &st, &counts,
+                         &Yc, stream);
+    } else {
+        rc = step_begin(ws, graph->csr.n, K, &st, &counts, &Yc, stream, L);
+        if (rc == GEE_OK && graph->csr.n > 0) {
+            ProfScope p("k_labels_multi", stream);
+            GEE_CHECK_CUDA(launch_labels_multi(Y, graph->csr.n, L, K,
+                                               graph->csr.rank, Yc, counts, st,
+                                               stream));
+        }
+    }
     if (rc != GEE_OK)
         return rc;
     rc = pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
-                   stream);
+                   stream, L);
     if (rc != GEE_OK)
         return rc;
     return read_status(st, stream);
@@ -643,6 +662,26 @@ gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
     return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
+}
+
+gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
+                                 int32_t L, int32_t K, int32_t laplacian,
+                                 float *Z, const gee_options *opts,
+                                 gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (graph == nullptr || L < 1)
+        return GEE_ERR_INVALID_ARG;
+    const gee_options o = resolve_options(opts);
+    gee_status rc = check_common(0, graph->csr.n, K, o.block);
+    if (rc != GEE_OK)
+        return rc;
+    if ((int64_t)L * K > GEE_MAX_COLUMNS)
+        return GEE_ERR_UNSUPPORTED;
+    if (graph->csr.n > 0 && (Y == nullptr || Z == nullptr))
+        return GEE_ERR_INVALID_ARG;
+    Workspace ws(stream);
+    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, L);
 }
 
 gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,

@@ -82,6 +82,47 @@ __global__ void __launch_bounds__(kLabelThreads)
             atomicAdd(&counts[k], hist[k]);
 }
 
+// L label vectors at once (Y[l*n + i]): the compact label of node i for
+// vector l goes to Yc[rank[i]*Ls + l] (Ls = label_stride(L); padding bytes
+// get 255), so one gather of adjacent bytes serves all vectors;
+// counts[l*K + k] = n_k of vector l.
+__global__ void k_labels_multi(const int32_t *__restrict__ Y, int64_t n,
+                               int32_t L, int32_t Ls, int32_t K,
+                               const int32_t *__restrict__ rank,
+                               uint8_t *__restrict__ Yc,
+                               uint32_t *__restrict__ counts, DevStatus *st)
+{
+    __shared__ uint32_t hist[GEE_MAX_COLUMNS];
+    for (int k = threadIdx.x; k < L * K; k += blockDim.x)
+        hist[k] = 0;
+    __syncthreads();
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int l = 0; l < L; ++l) {
+        const int32_t *Yl = Y + (int64_t)l * n;
+        for (int64_t i = tid; i < n; i += nthreads) {
+            const int32_t y = __ldcs(Yl + i);
+            uint32_t code = kNoLabel;
+            if ((uint32_t)y < (uint32_t)K) {
+                atomicAdd(&hist[l * K + y], 1u);
+                code = (uint32_t)y;
+            } else if (y != -1) {
+                report(st, GEE_ERR_LABEL_RANGE,
+                       (unsigned long long)(l * n + i));
+            }
+            const int64_t r = rank == nullptr ? i : (int64_t)rank[i];
+            Yc[r * Ls + l] = (uint8_t)code;
+            if (l == L - 1)
+                for (int p = L; p < Ls; ++p)
+                    Yc[r * Ls + p] = (uint8_t)kNoLabel;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < L * K; k += blockDim.x)
+        if (hist[k] != 0u)
+            atomicAdd(&counts[k], hist[k]);
+}
+
 // Calls f(u, v, edge_index) for every edge; two edges per 16-byte load when
 // E is 16-byte aligned.
 template <class F>
@@ -371,6 +412,19 @@ cudaError_t launch_labels(const int32_t *Y, int64_t n, int32_t K,
     const int blocks = grid_for((n + 3) / 4, kLabelThreads, sm_count() * 8);
     k_labels<<<blocks, kLabelThreads, 0, stream>>>(Y, n, K, rank, Yc, counts,
                                                    st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_multi(const int32_t *Y, int64_t n, int32_t L,
+                                int32_t K, const int32_t *rank, uint8_t *Yc,
+                                uint32_t *counts, DevStatus *st,
+                                cudaStream_t stream)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const int blocks = grid_for(n, kLabelThreads, sm_count() * 8);
+    k_labels_multi<<<blocks, kLabelThreads, 0, stream>>>(
+        Y, n, L, label_stride(L), K, rank, Yc, counts, st);
     return cudaGetLastError();
 }
 

@@ -542,8 +542,11 @@ struct PullArgs {
     uint32_t *hub_part;
     unsigned long long *work;
     const DevStatus *st;
-    int32_t K;
-    uint32_t kmagic;      // floor((2^32-1) / K) + 1: j / K == umulhi(j, kmagic)
+    int32_t cols;         // Z columns per row: L label vectors x classes
+    int32_t L;            // label vectors
+    int32_t Ls;           // bytes per rank in Yc: L padded to 4 or to 16
+    int32_t classes;      // classes per label vector
+    uint32_t kmagic;      // floor((2^32-1) / cols) + 1: j / cols == umulhi(j, kmagic)
     int32_t max_rows;
     int32_t area_off;     // start of the per-group / per-warp areas
     int32_t group_bytes;  // per group (light) or per warp (heavy)
@@ -562,13 +565,14 @@ __device__ __forceinline__ uint32_t label_of(const PullArgs &a, int32_t v)
     return __ldg(a.Yc + v);
 }
 
-// class of local cell j (the tile's first cell is a multiple of K); the
-// magic multiplier is exact for j < 2^32 / K and does not exist for K = 1
+// column of local cell j (the tile's first cell is a multiple of cols);
+// the magic multiplier is exact for j < 2^32 / cols and does not exist for
+// cols = 1
 __device__ __forceinline__ int class_of(const PullArgs &a, int j)
 {
-    if (a.K == 1)
+    if (a.cols == 1)
         return 0;
-    return j - a.K * (int)__umulhi((unsigned)j, a.kmagic);
+    return j - a.cols * (int)__umulhi((unsigned)j, a.kmagic);
 }
 
 template <bool WEIGHTED>
@@ -588,10 +592,10 @@ template <bool WEIGHTED>
 __device__ __forceinline__ void load_shared(const PullArgs &a, uint32_t *nk,
                                             float *table)
 {
-    for (int k = threadIdx.x; k < a.K; k += blockDim.x)
+    for (int k = threadIdx.x; k < a.cols; k += blockDim.x)
         nk[k] = a.counts[k];
     if (!WEIGHTED)
-        for (int i = threadIdx.x; i < a.K * kTableCounts; i += blockDim.x) {
+        for (int i = threadIdx.x; i < a.cols * kTableCounts; i += blockDim.x) {
             const int k = i / kTableCounts;
             table[i] = count_to_z((uint32_t)(i - k * kTableCounts),
                                   a.counts[k]);
@@ -600,12 +604,9 @@ __device__ __forceinline__ void load_shared(const PullArgs &a, uint32_t *nk,
 
 // Accumulator cells of a hub chunk: every arc belongs to the same row.
 struct ChunkCells {
-    int base;
+    int first;
     __device__ __forceinline__ void at(int) {}
-    __device__ __forceinline__ int cell(int, uint32_t y) const
-    {
-        return base + (int)y;
-    }
+    __device__ __forceinline__ int base(int) const { return first; }
 };
 
 // Accumulator cells of a row tile: rp[r] is the first arc of local row r
@@ -628,13 +629,13 @@ struct TileCells {
         row = lo;
         next = rp[lo + 1];
     }
-    __device__ __forceinline__ int cell(int i, uint32_t y)
+    __device__ __forceinline__ int base(int i)
     {
         while (i >= next) {
             ++row;
             next = rp[row + 1];
         }
-        return off + row * K + (int)y;
+        return off + row * K;
     }
 };
 
@@ -644,7 +645,7 @@ struct TileCells {
 // single arcs for the head and tail.  cells maps (arc, label) to an
 // accumulator index; arcs whose label is unknown go to this thread's own
 // sink cell (no branch, no shared-address contention).
-template <bool WEIGHTED, int NT, class Cells>
+template <bool WEIGHTED, bool MULTI, int NT, class Cells>
 __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            const int32_t *colp,
                                            const float *valp, int NA, int t,
@@ -652,18 +653,53 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            Cells &cells)
 {
     float *accf = reinterpret_cast<float *>(acc);
-    auto add = [&](int i, uint32_t y, float w) {
-        const int c = y != kNoLabel ? cells.cell(i, y) : sink;
+    auto put = [&](int c, float w) {
         if (WEIGHTED)
             atomicAdd(accf + c, w);
         else
             atomicAdd(acc + c, 1u);
     };
+    // one label vector: y is the target's label; several: y is the target
+    // rank and its L labels (adjacent bytes of Yc) are read here
+    auto add = [&](int i, uint32_t y, float w) {
+        if (!MULTI) {
+            put(y != kNoLabel ? cells.base(i) + (int)y : sink, w);
+        } else {
+            // the target's labels: Ls adjacent bytes, read 16 or 4 at a time
+            const int b = cells.base(i);
+            const uint8_t *lab = a.Yc + (int64_t)y * a.Ls;
+            auto four = [&](uint32_t word, int l0) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int l = l0 + e;
+                    const uint32_t yl = (word >> (8 * e)) & 0xFFu;
+                    if (l < a.L)
+                        put(yl != kNoLabel ? b + l * a.classes + (int)yl : sink,
+                            w);
+                }
+            };
+            if ((a.Ls & 15) == 0) {
+                for (int c = 0; c < a.Ls; c += 16) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(lab + c));
+                    four(q.x, c);
+                    four(q.y, c + 4);
+                    four(q.z, c + 8);
+                    four(q.w, c + 12);
+                }
+            } else {
+                for (int c = 0; c < a.Ls; c += 4)
+                    four(__ldg(reinterpret_cast<const uint32_t *>(lab + c)), c);
+            }
+        }
+    };
+    auto fetch = [&](int32_t v) -> uint32_t {
+        return MULTI ? (uint32_t)v : label_of(a, v);
+    };
     const int head =
         min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
     if (t < head) {
         cells.at(t);
-        add(t, label_of(a, colp[t]), WEIGHTED ? valp[t] : 0.0f);
+        add(t, fetch(colp[t]), WEIGHTED ? valp[t] : 0.0f);
     }
     const int nq = (NA - head) >> 2;
     const int4 *col4 = reinterpret_cast<const int4 *>(colp + head);
@@ -683,10 +719,10 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
         uint32_t y[kUnroll];
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
-            y[4 * u + 0] = label_of(a, c[u].x);
-            y[4 * u + 1] = label_of(a, c[u].y);
-            y[4 * u + 2] = label_of(a, c[u].z);
-            y[4 * u + 3] = label_of(a, c[u].w);
+            y[4 * u + 0] = fetch(c[u].x);
+            y[4 * u + 1] = fetch(c[u].y);
+            y[4 * u + 2] = fetch(c[u].z);
+            y[4 * u + 3] = fetch(c[u].w);
         }
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
@@ -709,18 +745,18 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
     const int tail0 = head + 4 * nq;
     if (t < NA - tail0) {
         cells.at(tail0 + t);
-        add(tail0 + t, label_of(a, colp[tail0 + t]),
+        add(tail0 + t, fetch(colp[tail0 + t]),
             WEIGHTED ? valp[tail0 + t] : 0.0f);
     }
 }
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, bool MULTI>
 __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                                          unsigned char *gs,
                                          const uint32_t *nk,
                                          const float *table, int64_t t)
 {
-    const int32_t K = a.K;
+    const int32_t K = a.cols;  // cells per row
     const int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
     if (r0 == r1)
         return;
@@ -747,7 +783,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     // sweep: the row of arc i is the last row starting at or before i
     if (NA > 0) {
         TileCells cells{rp, NR, K, off, 0, 0};
-        sweep_arcs<WEIGHTED, kGroupThreads>(
+        sweep_arcs<WEIGHTED, MULTI, kGroupThreads>(
             a, a.col + A0, WEIGHTED ? a.val + A0 : nullptr, NA, gt, acc,
             a.max_rows * K + 8 + (gt & 31), cells);
     }
@@ -788,7 +824,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     }
 }
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, bool MULTI>
 __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     k_pull_light(PullArgs a)
 {
@@ -796,7 +832,7 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     if (failed(a.st))
         return;
     uint32_t *nk = reinterpret_cast<uint32_t *>(sm);
-    float *table = reinterpret_cast<float *>(nk + 256);
+    float *table = reinterpret_cast<float *>(sm + ((a.cols * 4 + 15) & ~15));
     load_shared<WEIGHTED>(a, nk, table);
     __syncthreads();
     const int g = threadIdx.x / kGroupThreads;
@@ -810,21 +846,21 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
         const int64_t item = slot[it & 1];
         if (item >= a.ntiles)
             break;
-        row_tile<WEIGHTED>(a, g, gt, gs, nk, table, item);
+        row_tile<WEIGHTED, MULTI>(a, g, gt, gs, nk, table, item);
     }
 }
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, bool MULTI>
 __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     if (failed(a.st))
         return;
     uint32_t *nk = reinterpret_cast<uint32_t *>(sm);
-    float *table = reinterpret_cast<float *>(nk + 256);
+    float *table = reinterpret_cast<float *>(sm + ((a.cols * 4 + 15) & ~15));
     load_shared<WEIGHTED>(a, nk, table);
     __syncthreads();
-    const int32_t K = a.K;
+    const int32_t K = a.cols;  // cells per row
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint32_t *acc = reinterpret_cast<uint32_t *>(sm + a.area_off +
@@ -857,7 +893,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         const int64_t hend = a.hub_ptr[h + 1];
         const int n = (int)((b + kHubChunk < hend ? b + kHubChunk : hend) - b);
         ChunkCells cells{copy};
-        sweep_arcs<WEIGHTED, 32>(a, a.col_h + b,
+        sweep_arcs<WEIGHTED, MULTI, 32>(a, a.col_h + b,
                                  WEIGHTED ? a.val_h + b : nullptr, n, lane,
                                  acc, kHeavyCopies * K + lane, cells);
         __syncwarp();
@@ -924,21 +960,12 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
 
 inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-int optin_smem()
-{
-    int optin = 0, dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                               dev) != cudaSuccess)
-        optin = 227 * 1024;
-    return optin;
-}
-
-// Shared memory: [n_k (256)][table 256 x 8][per-group / per-warp areas].
+// Shared memory: [n_k (cols)][table cols x 8][per-group / per-warp areas].
 // Returns the bytes to launch with.
 size_t plan_shared(size_t area_bytes, PullArgs &a)
 {
-    const size_t fixed = 256 * 4 + 256 * kTableCounts * 4;
+    const size_t fixed = align16((size_t)a.cols * 4) +
+                         align16((size_t)a.cols * kTableCounts * 4);
     a.area_off = (int32_t)fixed;
     return fixed + area_bytes;
 }
@@ -1128,7 +1155,8 @@ static cudaError_t launch_persistent(Kern kernel, int threads, size_t smem,
     return cudaGetLastError();
 }
 
-static PullArgs pull_args(const Csr &g, int32_t K, bool laplacian,
+static PullArgs pull_args(const Csr &g, int32_t L, int32_t classes,
+                          bool laplacian,
                           const int32_t *tile_row, int64_t ntiles,
                           const uint8_t *Yc, const uint32_t *counts, float *Z,
                           void *hub_part, unsigned long long *work,
@@ -1155,13 +1183,18 @@ static PullArgs pull_args(const Csr &g, int32_t K, bool laplacian,
     a.hub_part = static_cast<uint32_t *>(hub_part);
     a.work = work;
     a.st = st;
-    a.K = K;
-    a.kmagic = K > 1 ? (uint32_t)(0xFFFFFFFFull / (uint32_t)K + 1ull) : 0u;
+    a.L = L;
+    a.Ls = label_stride(L);
+    a.classes = classes;
+    a.cols = L * classes;
+    a.kmagic = a.cols > 1 ? (uint32_t)(0xFFFFFFFFull / (uint32_t)a.cols + 1ull)
+                          : 0u;
     return a;
 }
 
-cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
-                              bool laplacian, const int32_t *tile_row,
+cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
+                              bool weighted, bool laplacian,
+                              const int32_t *tile_row,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
@@ -1169,8 +1202,9 @@ cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
 {
     if (ntiles == 0)
         return cudaSuccess;
-    PullArgs a = pull_args(g, K, laplacian, tile_row, ntiles, Yc, counts, Z,
-                           nullptr, work, st);
+    PullArgs a = pull_args(g, L, classes, laplacian, tile_row, ntiles, Yc,
+                           counts, Z, nullptr, work, st);
+    const int K = a.cols;
     const int C = row_cost(K);
     a.max_rows = (kTileUnits + C - 1) / C;
     const size_t rpb = align16((size_t)(a.max_rows + 2) * 4);
@@ -1184,32 +1218,44 @@ cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess)
         return e;
-    return (weighted || laplacian)
-               ? launch_persistent(k_pull_light<true>, kGroups * kGroupThreads,
-                                   smem, a, stream)
-               : launch_persistent(k_pull_light<false>, kGroups * kGroupThreads,
-                                   smem, a, stream);
+    const int threads = kGroups * kGroupThreads;
+    const bool w = weighted || laplacian;
+    if (L > 1)
+        return w ? launch_persistent(k_pull_light<true, true>, threads, smem,
+                                     a, stream)
+                 : launch_persistent(k_pull_light<false, true>, threads, smem,
+                                     a, stream);
+    return w ? launch_persistent(k_pull_light<true, false>, threads, smem, a,
+                                 stream)
+             : launch_persistent(k_pull_light<false, false>, threads, smem, a,
+                                 stream);
 }
 
-cudaError_t launch_pull_heavy(const Csr &g, int32_t K, bool weighted,
-                              bool laplacian, const uint8_t *Yc,
+cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
+                              bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               void *hub_part, const DevStatus *st,
                               cudaStream_t stream)
 {
     if (g.chunks == 0)
         return cudaSuccess;
-    PullArgs a = pull_args(g, K, laplacian, nullptr, 0, Yc, counts, Z,
+    PullArgs a = pull_args(g, L, classes, laplacian, nullptr, 0, Yc, counts, Z,
                            hub_part, nullptr, st);
-    // kHeavyCopies accumulators of K cells, then 32 sink cells
-    a.group_bytes = (int32_t)align16((size_t)(kHeavyCopies * K + 32) * 4);
+    // kHeavyCopies accumulators of cols cells, then 32 sink cells
+    a.group_bytes =
+        (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);
     const size_t smem =
         plan_shared((size_t)(kHeavyThreads / 32) * a.group_bytes, a);
-    return (weighted || laplacian)
-               ? launch_persistent(k_pull_heavy<true>, kHeavyThreads, smem, a,
-                                   stream)
-               : launch_persistent(k_pull_heavy<false>, kHeavyThreads, smem, a,
-                                   stream);
+    const bool w = weighted || laplacian;
+    if (L > 1)
+        return w ? launch_persistent(k_pull_heavy<true, true>, kHeavyThreads,
+                                     smem, a, stream)
+                 : launch_persistent(k_pull_heavy<false, true>, kHeavyThreads,
+                                     smem, a, stream);
+    return w ? launch_persistent(k_pull_heavy<true, false>, kHeavyThreads, smem,
+                                 a, stream)
+             : launch_persistent(k_pull_heavy<false, false>, kHeavyThreads, smem,
+                                 a, stream);
 }
 
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,

@@ -109,6 +109,15 @@ cudaError_t launch_status_init(DevStatus *st, cudaStream_t stream);
 cudaError_t launch_labels(const int32_t *Y, int64_t n, int32_t K,
                           const int32_t *rank, uint8_t *Yc, uint32_t *counts,
                           DevStatus *st, cudaStream_t stream);
+// Bytes per node of the multi-label compact array: L padded to 4, or to a
+// multiple of 16 above 8, so a node's labels load as whole words.
+inline int label_stride(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : (L + 15) & ~15); }
+// The same for L label vectors Y[l*n + i]: Yc[rank[i]*Ls + l] (padding
+// bytes hold 255, "unknown") and counts[l*K + k]; L*K <= GEE_MAX_COLUMNS.
+cudaError_t launch_labels_multi(const int32_t *Y, int64_t n, int32_t L,
+                                int32_t K, const int32_t *rank, uint8_t *Yc,
+                                uint32_t *counts, DevStatus *st,
+                                cudaStream_t stream);
 
 cudaError_t launch_validate_edges(const int32_t *E, int64_t s, int64_t n,
                                   DevStatus *st, cudaStream_t stream);
@@ -198,14 +207,16 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 // with several chunks.  Yc is in rank order.  hub_part: scratch
 // [chunks * K] of 4-byte per-chunk partial sums; work: one 8-byte scratch
 // counter.
-cudaError_t launch_pull_light(const Csr &g, int32_t K, bool weighted,
-                              bool laplacian, const int32_t *tile_row,
+// K arguments of the CSR launches count Z columns (L vectors x classes).
+cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
+                              bool weighted, bool laplacian,
+                              const int32_t *tile_row,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
                               cudaStream_t stream);
-cudaError_t launch_pull_heavy(const Csr &g, int32_t K, bool weighted,
-                              bool laplacian, const uint8_t *Yc,
+cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
+                              bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               void *hub_part, const DevStatus *st,
                               cudaStream_t stream);

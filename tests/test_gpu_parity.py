@@ -218,3 +218,45 @@ def test_relabeling_a_resident_graph(gee, rmat16):
             Y = graphgen.labels(n, K, seed=1000 + seed, frac_unlabeled=0.1 * seed)
             got = g.embed(_dev(Y), K).cpu().numpy()
             assert np.array_equal(got, oracle.embed_counts32(edges, Y, K))
+
+
+@pytest.mark.parametrize("L,K", [(2, 5), (3, 50), (32, 20), (4, 255)])
+def test_multi_label_pass_equals_single_passes(gee, rmat16, L, K):
+    """L label vectors in one pass (W widened to L*K columns): each block of
+    K columns equals the oracle's embedding for that vector."""
+    import torch
+    edges, n = rmat16
+    Ys = np.stack([graphgen.labels(n, K, seed=500 + l, frac_unlabeled=0.05 * (l % 3))
+                   for l in range(L)])
+    with gee.Graph(_dev(edges), n) as g:
+        Z = g.embed_multi(_dev(Ys), K).cpu().numpy()
+    assert Z.shape == (n, L * K)
+    for l in (0, L // 2, L - 1):
+        want = oracle.embed_counts32(edges, Ys[l], K)
+        assert np.array_equal(Z[:, l * K:(l + 1) * K], want), l
+
+
+def test_multi_label_weighted_laplacian(gee):
+    n, s, K, L = 3000, 60000, 7, 5
+    edges = graphgen.random_graph(n, s, seed=61)
+    w = graphgen.weights(s, seed=62)
+    Ys = np.stack([graphgen.labels(n, K, seed=63 + l, frac_unlabeled=0.1) for l in range(L)])
+    with gee.Graph(_dev(edges), n, weights=_dev(w)) as g:
+        for lap in (False, True):
+            Z = g.embed_multi(_dev(Ys), K, laplacian=lap).cpu().numpy()
+            for l in range(L):
+                want = oracle.embed(edges, Ys[l], K, weights=w, laplacian=lap)
+                assert_weighted_close(Z[:, l * K:(l + 1) * K], want, f"multi-{l}-{lap}")
+
+
+def test_multi_label_limits(gee, tiny_sbm_graph):
+    edges, Y = tiny_sbm_graph
+    with gee.Graph(_dev(edges), Y.size) as g:
+        Ys = np.stack([Y] * 5)
+        with pytest.raises(gee.GeeError) as ei:
+            g.embed_multi(_dev(Ys), 255)  # 5 * 255 columns > 1024
+        assert ei.value.name == "GEE_ERR_UNSUPPORTED"
+        Ys[3, 17] = 9
+        with pytest.raises(gee.GeeError) as ei:
+            g.embed_multi(_dev(Ys), 5)
+        assert ei.value.name == "GEE_ERR_LABEL_RANGE"
