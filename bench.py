@@ -318,6 +318,15 @@ def run_multi(args, w, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     ms = max_over_ranks(e0.elapsed_time(e1), world) / args.steps
+    # per-kernel times of a few more passes (launch tracing, after the timed region)
+    gee.profile_read()
+    gee.profile_enable(True)
+    for _ in range(3):
+        g.embed_multi(Ys, K, laplacian=lap, out=Zm)
+    torch.cuda.synchronize()
+    gee.profile_enable(False)
+    kernels = {k: {"launches": v["launches"], "ms": v["total_ms"] / 3}
+               for k, v in gee.profile_read().items()}
     # same results in both forms: compare two blocks with single-vector calls
     worst = 0.0
     for l in (0, L - 1):
@@ -344,6 +353,7 @@ def run_multi(args, w, world, rank, local):
         "plain": {"value": world * L * s / (plain_ms / 1e3), "ms_for_L_calls": plain_ms,
                   "api": "L x gee_embed_graph"},
         "speedup_vs_plain": plain_ms / ms,
+        "kernels_per_pass": kernels,
         "max_rel_diff_vs_plain": worst,
     }
     g.close()

@@ -204,6 +204,30 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                      const DevStatus *st, cudaStream_t stream, int32_t L = 1)
 {
     const int32_t cols = L * K;
+    if (L >= kWideMinLabels) {
+        unsigned long long *work = nullptr;
+        void *hub_part = nullptr;
+        GEE_CHECK_CUDA(ws.alloc((void **)&work, sizeof(unsigned long long)));
+        GEE_CHECK_CUDA(
+            ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
+        {
+            ProfScope p("k_wide_rows", stream);
+            GEE_CHECK_CUDA(launch_wide_rows(g, L, K, g.weighted, laplacian, Yc,
+                                            counts, Z, work, st, stream));
+        }
+        if (g.chunks > 0) {
+            ProfScope p("k_wide_chunks", stream);
+            GEE_CHECK_CUDA(launch_wide_chunks(g, L, K, g.weighted, laplacian,
+                                              Yc, counts, Z, hub_part, st,
+                                              stream));
+        }
+        if (g.hubs > 0) {
+            ProfScope p("k_hub_fixup", stream);
+            GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
+                                            counts, Z, hub_part, st, stream));
+        }
+        return GEE_OK;
+    }
     const int64_t ntiles = pull_tiles(g, cols);
     int32_t *tile_row = nullptr;
     void *hub_part = nullptr;

@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(kLabelThreads)
 // L label vectors at once (Y[l*n + i]): the compact label of node i for
 // vector l goes to Yc[rank[i]*Ls + l] (Ls = label_stride(L); padding bytes
 // get 255), so one gather of adjacent bytes serves all vectors;
-// counts[l*K + k] = n_k of vector l.
+// counts[l*K + k] = n_k of vector l.  One thread per node reads its L
+// labels (coalesced across the warp for each l) and writes its record with
+// whole-word stores: 4, 8 or 16 bytes at a time.
 __global__ void k_labels_multi(const int32_t *__restrict__ Y, int64_t n,
                                int32_t L, int32_t Ls, int32_t K,
                                const int32_t *__restrict__ rank,
@@ -98,23 +100,44 @@ __global__ void k_labels_multi(const int32_t *__restrict__ Y, int64_t n,
     __syncthreads();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int l = 0; l < L; ++l) {
-        const int32_t *Yl = Y + (int64_t)l * n;
-        for (int64_t i = tid; i < n; i += nthreads) {
-            const int32_t y = __ldcs(Yl + i);
+    // codes of labels l0 .. l0+15 of node i (255 beyond L) packed in four
+    // words; all loads are issued before the histogram updates
+    auto codes16 = [&](int l0, int64_t i, uint32_t (&word)[4]) {
+        int32_t y[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            y[e] = l0 + e < L ? __ldcs(Y + (int64_t)(l0 + e) * n + i) : -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            word[q] = 0u;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
             uint32_t code = kNoLabel;
-            if ((uint32_t)y < (uint32_t)K) {
-                atomicAdd(&hist[l * K + y], 1u);
-                code = (uint32_t)y;
-            } else if (y != -1) {
+            if ((uint32_t)y[e] < (uint32_t)K) {
+                atomicAdd(&hist[(l0 + e) * K + y[e]], 1u);
+                code = (uint32_t)y[e];
+            } else if (y[e] != -1) {
                 report(st, GEE_ERR_LABEL_RANGE,
-                       (unsigned long long)(l * n + i));
+                       (unsigned long long)((l0 + e) * n + i));
             }
-            const int64_t r = rank == nullptr ? i : (int64_t)rank[i];
-            Yc[r * Ls + l] = (uint8_t)code;
-            if (l == L - 1)
-                for (int p = L; p < Ls; ++p)
-                    Yc[r * Ls + p] = (uint8_t)kNoLabel;
+            word[e >> 2] |= code << (8 * (e & 3));
+        }
+    };
+    for (int64_t i = tid; i < n; i += nthreads) {
+        const int64_t r = rank == nullptr ? i : (int64_t)rank[i];
+        uint8_t *rec = Yc + r * Ls;
+        uint32_t word[4];
+        if (Ls <= 8) {
+            codes16(0, i, word);
+            *reinterpret_cast<uint32_t *>(rec) = word[0];
+            if (Ls == 8)
+                *reinterpret_cast<uint32_t *>(rec + 4) = word[1];
+        } else {
+            for (int c = 0; c < Ls; c += 16) {
+                codes16(c, i, word);
+                *reinterpret_cast<uint4 *>(rec + c) =
+                    make_uint4(word[0], word[1], word[2], word[3]);
+            }
         }
     }
     __syncthreads();

@@ -109,9 +109,14 @@ cudaError_t launch_status_init(DevStatus *st, cudaStream_t stream);
 cudaError_t launch_labels(const int32_t *Y, int64_t n, int32_t K,
                           const int32_t *rank, uint8_t *Yc, uint32_t *counts,
                           DevStatus *st, cudaStream_t stream);
-// Bytes per node of the multi-label compact array: L padded to 4, or to a
-// multiple of 16 above 8, so a node's labels load as whole words.
-inline int label_stride(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : (L + 15) & ~15); }
+// Bytes per node of the multi-label compact array: L padded to 4 or 8 for
+// fewer than kWideMinLabels vectors, else to a multiple of 32 (one L2 sector
+// per block of 32 labels), so a node's labels load as whole words.
+constexpr int kWideMinLabels = 8;
+inline int label_stride(int L)
+{
+    return L <= 4 ? 4 : (L < kWideMinLabels ? 8 : (L + 31) & ~31);
+}
 // The same for L label vectors Y[l*n + i]: Yc[rank[i]*Ls + l] (padding
 // bytes hold 255, "unknown") and counts[l*K + k]; L*K <= GEE_MAX_COLUMNS.
 cudaError_t launch_labels_multi(const int32_t *Y, int64_t n, int32_t L,
@@ -224,6 +229,21 @@ cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
                              const void *hub_part, const DevStatus *st,
                              cudaStream_t stream);
+
+// S4 + S5 (CSR form) for many label vectors (gee_wide.cu): the lanes of a
+// warp take the labels of one arc.  Same order and contract as the three
+// launches above, with launch_hub_fixup(g, L*K, ...) last; no row tiles.
+// For L >= kWideMinLabels.
+cudaError_t launch_wide_rows(const Csr &g, int32_t L, int32_t K,
+                             bool weighted, bool laplacian, const uint8_t *Yc,
+                             const uint32_t *counts, float *Z,
+                             unsigned long long *work, const DevStatus *st,
+                             cudaStream_t stream);
+cudaError_t launch_wide_chunks(const Csr &g, int32_t L, int32_t K,
+                               bool weighted, bool laplacian,
+                               const uint8_t *Yc, const uint32_t *counts,
+                               float *Z, void *hub_part, const DevStatus *st,
+                               cudaStream_t stream);
 
 // ------------------------------------------------------------ tracing
 // When tracing is on (gee_profile_enable), a ProfScope brackets one kernel

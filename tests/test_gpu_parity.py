@@ -220,10 +220,15 @@ def test_relabeling_a_resident_graph(gee, rmat16):
             assert np.array_equal(got, oracle.embed_counts32(edges, Y, K))
 
 
-@pytest.mark.parametrize("L,K", [(2, 5), (3, 50), (32, 20), (4, 255)])
+@pytest.mark.parametrize("L,K", [(2, 5), (3, 50), (4, 255), (7, 9),
+                                 (8, 3), (16, 64), (32, 20), (33, 31),
+                                 (64, 16), (256, 4)])
 def test_multi_label_pass_equals_single_passes(gee, rmat16, L, K):
     """L label vectors in one pass (W widened to L*K columns): each block of
-    K columns equals the oracle's embedding for that vector."""
+    K columns equals the oracle's embedding for that vector.  Covers both
+    forms of the pass (one lane per arc below 8 vectors, one lane per label
+    vector from 8 on), one and several blocks of 32 vectors, odd and even K,
+    and the 1,024-column limit."""
     import torch
     edges, n = rmat16
     Ys = np.stack([graphgen.labels(n, K, seed=500 + l, frac_unlabeled=0.05 * (l % 3))
@@ -236,17 +241,43 @@ def test_multi_label_pass_equals_single_passes(gee, rmat16, L, K):
         assert np.array_equal(Z[:, l * K:(l + 1) * K], want), l
 
 
-def test_multi_label_weighted_laplacian(gee):
-    n, s, K, L = 3000, 60000, 7, 5
-    edges = graphgen.random_graph(n, s, seed=61)
+@pytest.mark.parametrize("L,K", [(5, 7), (12, 6), (12, 8), (40, 3), (33, 4)])
+def test_multi_label_weighted_laplacian(gee, L, K):
+    """Weighted and Laplacian multi-label passes on an R-MAT graph whose hub
+    rows span several chunks; from 8 vectors on the pass sums each cell in
+    one lane, so repeated calls agree bit for bit."""
+    n, s = 5000, 150000
+    edges = graphgen.rmat_edges(13, n, 0, s, seed=61)
+    assert np.bincount(edges.ravel(), minlength=n).max() > 2 * 2048
     w = graphgen.weights(s, seed=62)
     Ys = np.stack([graphgen.labels(n, K, seed=63 + l, frac_unlabeled=0.1) for l in range(L)])
     with gee.Graph(_dev(edges), n, weights=_dev(w)) as g:
         for lap in (False, True):
             Z = g.embed_multi(_dev(Ys), K, laplacian=lap).cpu().numpy()
-            for l in range(L):
+            for l in sorted({0, 1, L // 2, L - 1}):
                 want = oracle.embed(edges, Ys[l], K, weights=w, laplacian=lap)
                 assert_weighted_close(Z[:, l * K:(l + 1) * K], want, f"multi-{l}-{lap}")
+            if L >= 8:
+                again = g.embed_multi(_dev(Ys), K, laplacian=lap).cpu().numpy()
+                assert np.array_equal(Z.view(np.uint32), again.view(np.uint32))
+
+
+def test_multi_label_unaligned_output(gee, rmat16):
+    """A Z that is not 16-byte aligned takes the transposing write of the
+    multi-label pass; the result is the same as with an aligned Z."""
+    import torch
+    edges, n = rmat16
+    L, K = 16, 8
+    Ys = np.stack([graphgen.labels(n, K, seed=900 + l, frac_unlabeled=0.1)
+                   for l in range(L)])
+    with gee.Graph(_dev(edges), n) as g:
+        aligned = g.embed_multi(_dev(Ys), K).cpu().numpy()
+        buf = torch.empty(n * L * K + 1, dtype=torch.float32, device="cuda")
+        Z = buf[1:].view(n, L * K)
+        g.embed_multi(_dev(Ys), K, out=Z)
+        assert np.array_equal(Z.cpu().numpy(), aligned)
+    want = oracle.embed_counts32(edges, Ys[L - 1], K)
+    assert np.array_equal(aligned[:, (L - 1) * K:], want)
 
 
 def test_multi_label_limits(gee, tiny_sbm_graph):
