@@ -39,6 +39,7 @@ TAG_LABEL = 0x4C41424C    # "LABL"
 TAG_WEIGHT = 0x57474854   # "WGHT"
 TAG_SBM = 0x53424D30      # "SBM0"
 TAG_SHUFFLE = 0x53484646  # "SHFF"
+TAG_PLANTED = 0x504C4E54  # "PLNT"
 
 RMAT_MAX_ATTEMPTS = 64
 # odd multipliers of the id bijection (any odd constants work)
@@ -228,6 +229,52 @@ def tiny_sbm(seed=1):
     return sbm([2000] * 5, 0.02, 0.002, seed)
 
 
+def planted_block_start(g, n, K):
+    """First node of block g when n nodes are cut into K nearly equal blocks
+    (node i is in block floor(i K / n))."""
+    return (np.asarray(g, dtype=np.int64) * n + K - 1) // K
+
+
+def planted_labels(n, K):
+    """Block of every node: floor(i K / n)."""
+    return ((np.arange(n, dtype=np.int64) * K) // n).astype(np.int32)
+
+
+def planted_same_threshold(n, K, ratio):
+    """2^32 times the probability that an edge stays inside its first
+    endpoint's block, for p_in / p_out = ratio: ratio (b-1) / (ratio (b-1) +
+    n - b) with b = n / K, the share of a node's expected SBM edges that are
+    inside its block."""
+    b = n / K
+    inside = ratio * (b - 1.0)
+    q = 1.0 if n - b <= 0 else (inside / (inside + (n - b)) if inside > 0 else 0.0)
+    return min(int(q * 4294967296.0), 1 << 32)
+
+
+def planted_edges(n, K, s, ratio, seed, start=0):
+    """Edges [start, start+s) of a planted-partition graph drawn edge by
+    edge: the first endpoint uniform over the n nodes, the second inside its
+    block with probability planted_same_threshold / 2^32 (else uniform over
+    the other blocks).  The edge-sampling form of a K-block SBM with
+    p_in / p_out = ratio, for graphs too large to draw pair by pair.
+    (s, 2) int32."""
+    idx = np.arange(start, start + s, dtype=np.uint64)
+    x, y, z, _ = _words(idx, 0, TAG_PLANTED, seed)
+    nn = np.uint64(n)
+    u = (x.astype(np.uint64) * nn) >> np.uint64(32)
+    g = (u * np.uint64(K)) // nn
+    b0 = (g * nn + np.uint64(K - 1)) // np.uint64(K)
+    b1 = ((g + np.uint64(1)) * nn + np.uint64(K - 1)) // np.uint64(K)
+    size = b1 - b0
+    z64 = z.astype(np.uint64)
+    v_in = b0 + ((z64 * size) >> np.uint64(32))
+    r = (z64 * (nn - size)) >> np.uint64(32)
+    v_out = np.where(r < b0, r, r + size)
+    same = y.astype(np.uint64) < np.uint64(planted_same_threshold(n, K, ratio))
+    v = np.where(same, v_in, v_out)
+    return np.stack([u, v], axis=1).astype(np.int32)
+
+
 def random_graph(n, s, seed, self_loops=True):
     """Uniform random multigraph with s edges on n nodes (small tests)."""
     idx = np.arange(s, dtype=np.uint64)
@@ -277,7 +324,10 @@ def _lib():
             lib.graphgen_rmat.argtypes = [P, I64, I64, _ctypes.c_int, I64, U32, U32, U32, U64, P]
             lib.graphgen_labels.argtypes = [P, I64, I64, I32, U64, U64, P]
             lib.graphgen_weights.argtypes = [P, I64, I64, U64, P]
-            for f in (lib.graphgen_rmat, lib.graphgen_labels, lib.graphgen_weights):
+            lib.graphgen_planted.argtypes = [P, I64, I64, I64, I32, U64, U64, P]
+            lib.graphgen_planted_labels.argtypes = [P, I64, I32, P]
+            for f in (lib.graphgen_rmat, lib.graphgen_labels, lib.graphgen_weights,
+                      lib.graphgen_planted, lib.graphgen_planted_labels):
                 f.restype = _ctypes.c_int
             _dev_lib = lib
     return _dev_lib
@@ -322,4 +372,28 @@ def weights_device(s, seed, start=0, out=None, device="cuda"):
                                  int(seed) & 0xFFFFFFFFFFFFFFFF, _stream())
     if rc != 0:
         raise RuntimeError(f"graphgen_weights failed ({rc})")
+    return out
+
+
+def planted_edges_device(n, K, s, ratio, seed, start=0, out=None, device="cuda"):
+    """Same edges as planted_edges, drawn on the GPU."""
+    import torch
+    if out is None:
+        out = torch.empty((s, 2), dtype=torch.int32, device=device)
+    rc = _lib().graphgen_planted(_ctypes.c_void_p(out.data_ptr()), start, s, n, K,
+                                 planted_same_threshold(n, K, ratio),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, _stream())
+    if rc != 0:
+        raise RuntimeError(f"graphgen_planted failed ({rc})")
+    return out
+
+
+def planted_labels_device(n, K, out=None, device="cuda"):
+    """Same labels as planted_labels, written on the GPU."""
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=device)
+    rc = _lib().graphgen_planted_labels(_ctypes.c_void_p(out.data_ptr()), n, K, _stream())
+    if rc != 0:
+        raise RuntimeError(f"graphgen_planted_labels failed ({rc})")
     return out

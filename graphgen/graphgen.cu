@@ -17,6 +17,7 @@ constexpr uint32_t kTagRmat = 0x524D4154u;
 constexpr uint32_t kTagPerm = 0x5045524Du;
 constexpr uint32_t kTagLabel = 0x4C41424Cu;
 constexpr uint32_t kTagWeight = 0x57474854u;
+constexpr uint32_t kTagPlanted = 0x504C4E54u;
 constexpr int kMaxAttempts = 64;
 constexpr uint64_t kPermMul1 = 0x2545F491ull;
 constexpr uint64_t kPermMul2 = 0x9E3779B1ull;
@@ -140,6 +141,42 @@ __global__ void k_weights(float *__restrict__ out, int64_t start,
     }
 }
 
+// Planted partition drawn edge by edge (see planted_edges in Python).
+__global__ void k_planted(int2 *__restrict__ out, int64_t start, int64_t count,
+                          uint64_t n, uint64_t K, uint64_t thr, uint64_t seed)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int64_t i = tid; i < count; i += nthreads) {
+        const uint64_t idx = (uint64_t)(start + i);
+        const U4 w = philox((uint32_t)idx, (uint32_t)(idx >> 32), 0u,
+                            kTagPlanted, k0, k1);
+        const uint64_t u = ((uint64_t)w.x * n) >> 32;
+        const uint64_t g = (u * K) / n;
+        const uint64_t b0 = (g * n + K - 1) / K;
+        const uint64_t b1 = ((g + 1) * n + K - 1) / K;
+        const uint64_t size = b1 - b0;
+        uint64_t v;
+        if ((uint64_t)w.y < thr) {
+            v = b0 + (((uint64_t)w.z * size) >> 32);
+        } else {
+            const uint64_t r = ((uint64_t)w.z * (n - size)) >> 32;
+            v = r < b0 ? r : r + size;
+        }
+        out[i] = make_int2((int)u, (int)v);
+    }
+}
+
+__global__ void k_planted_labels(int32_t *__restrict__ out, int64_t n,
+                                 int64_t K)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nthreads)
+        out[i] = (int32_t)((i * K) / n);
+}
+
 int blocks_for(int64_t count)
 {
     int64_t b = (count + 255) / 256;
@@ -196,5 +233,31 @@ GG_API int graphgen_weights(void *out, int64_t start, int64_t count,
         return 0;
     k_weights<<<blocks_for(count), 256, 0, (cudaStream_t)stream>>>(
         static_cast<float *>(out), start, count, seed);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+GG_API int graphgen_planted(void *out, int64_t start, int64_t count, int64_t n,
+                            int32_t K, uint64_t thr, uint64_t seed,
+                            void *stream)
+{
+    if (count <= 0)
+        return 0;
+    if (n < 1 || n > 2147483647ll || K < 1 || K > n)
+        return 1;
+    k_planted<<<blocks_for(count), 256, 0, (cudaStream_t)stream>>>(
+        static_cast<int2 *>(out), start, count, (uint64_t)n, (uint64_t)K, thr,
+        seed);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+GG_API int graphgen_planted_labels(void *out, int64_t n, int32_t K,
+                                   void *stream)
+{
+    if (n <= 0)
+        return 0;
+    if (K < 1)
+        return 1;
+    k_planted_labels<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        static_cast<int32_t *>(out), n, K);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

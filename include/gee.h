@@ -11,9 +11,10 @@
  * (Alg. 1, loop body), i.e. Z = A W with A = M + M^T.
  *
  * Conventions shared by every entry point:
- *   - edges: int32 [s][2] row-major, (u, v) per edge, 0 <= u, v < n.  Each
- *     listed edge applies both updates (Section II: an undirected graph is
- *     two symmetric directed graphs; list each undirected edge once).  A
+ *   - edges: int32 [s][2] row-major, (u, v) per edge, 0 <= u, v < n,
+ *     8-byte aligned (one pair per load; GEE_ERR_INVALID_ARG otherwise).
+ *     Each listed edge applies both updates (Section II: an undirected graph
+ *     is two symmetric directed graphs; list each undirected edge once).  A
  *     self-loop adds 2w / n_k to Z[u, Y[u]].  Repeated edges add up.
  *   - weights: float32 [s] or NULL for unit weights (Section II).
  *   - Y: int32 [n]; 0..K-1 are classes, -1 means "class unknown" (the paper's
@@ -191,6 +192,129 @@ GEE_API gee_strategy gee_pick_strategy(int64_t s, int64_t n, int32_t K,
 GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
                            int32_t weighted, int32_t laplacian,
                            const gee_options *opts);
+
+/*
+ * Batched embedding: `count` independent problems, each with the arguments
+ * of gee_embed (its own edges, weights, Y, n, K and Z; no Laplacian), run
+ * by one sequence of persistent launches over all of them -- the batched
+ * form of Alg. 1 for many small graphs, which would each leave most of the
+ * GPU idle and pay several launches and a host round trip one call at a
+ * time.  Per problem the result equals gee_embed's: bit for bit with unit
+ * weights, within float32 summation order with weights.
+ *
+ * problems: host array [count]; the buffers it points to are device memory
+ * and must not overlap between problems (Z of one problem is written while
+ * others are read).  statuses: host array [count] filled with each
+ * problem's status, or NULL.  A problem whose labels or endpoints fail the
+ * device checks gets GEE_ERR_LABEL_RANGE / GEE_ERR_NODE_RANGE and its Z is
+ * left unmodified (with opts->validate_edges = 0, a bad endpoint is skipped,
+ * reported, and that problem's Z is undefined); the other problems are
+ * still computed.  Returns GEE_OK when every problem succeeded, else the
+ * status of the first failing problem (argument errors are found on the
+ * host before anything runs).  opts->strategy and opts->block are ignored.
+ */
+typedef struct gee_problem {
+    const int32_t *edges;    /* int32 [s][2], 8-byte aligned */
+    const float *weights;    /* float [s], or NULL for unit weights */
+    int64_t s;
+    const int32_t *Y;        /* int32 [n] */
+    int64_t n;
+    int32_t K;
+    int32_t reserved;        /* must be 0 */
+    float *Z;                /* float [n][K], written */
+} gee_problem;
+
+GEE_API gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
+                                   gee_status *statuses,
+                                   const gee_options *opts,
+                                   gee_stream_t stream);
+
+/*
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper, which embeds one graph per call).  Clients submit embedding
+ * requests -- an edge list with its labels, or a new label vector for a
+ * graph kept resident on the device (re-labeling, as in the unsupervised
+ * GEE loop) -- from any thread, and wait for them by ticket.  One scheduler
+ * thread admits requests in arrival order while the device memory they need
+ * fits in the budget (with the resident graphs), and launches them as soon
+ * as one of `streams` slots is free, so work that arrives while other
+ * requests run overlaps with them on the GPU:
+ *   - consecutive edge-list requests are fused into one gee_embed_batch
+ *     launch sequence (up to max_batch requests / max_batch_edges edges);
+ *   - re-labelings of the same resident graph with the same K and variant
+ *     waiting anywhere in the queue are fused into one multi-label pass
+ *     (W widened to L*K <= GEE_MAX_COLUMNS columns).
+ * Each request's Z equals the result of the corresponding plain call (bit
+ * for bit with unit weights; within float32 summation order and the
+ * multi-label pass's reciprocal scaling, far below 1e-5 relative, with
+ * weights).  Edge-list requests have no Laplacian variant here
+ * (GEE_ERR_UNSUPPORTED).
+ *
+ * Host buffers of a request (edges_h, weights_h, Y_h, Z_h) must stay valid
+ * until gee_server_wait returns for it; Z_h is written by then.  Page-locked
+ * host buffers let copies overlap with other requests' kernels; pageable
+ * ones work but make the scheduler wait for each copy.  If a request fails
+ * (its status is returned by gee_server_wait), its Z_h is unspecified.
+ */
+typedef struct gee_server gee_server;
+
+typedef struct gee_server_config {
+    int64_t hbm_budget_bytes;  /* device bytes for resident graphs plus the
+                                  requests in flight; 0: 80 GiB */
+    int32_t streams;           /* launch groups in flight at once, 1..16;
+                                  0: 4 */
+    int32_t max_batch;         /* requests per launch group, 1..4096; 0: 256 */
+    int64_t max_batch_edges;   /* edges per edge-list launch group; 0: 2^28 */
+    int64_t reserved[2];       /* must be 0 */
+} gee_server_config;
+
+typedef struct gee_request {
+    int64_t graph;             /* resident graph id, or -1 for an edge list */
+    const int32_t *edges_h;    /* graph == -1: int32 [s][2] */
+    const float *weights_h;    /* graph == -1: float [s] or NULL */
+    int64_t s;                 /* graph == -1: edges */
+    int64_t n;                 /* graph == -1: nodes (a resident graph has
+                                  its own n) */
+    const int32_t *Y_h;        /* int32 [n] */
+    int32_t K;
+    int32_t laplacian;         /* resident graphs only */
+    float *Z_h;                /* float [n][K], written on completion */
+} gee_request;
+
+typedef struct gee_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t groups;            /* launch groups */
+    int64_t batched_requests;  /* requests that shared a group with others */
+    int64_t max_group;         /* largest group */
+    int64_t max_concurrent;    /* most groups in flight at once */
+    int64_t resident_bytes;    /* estimated bytes of resident graphs */
+    int64_t peak_inflight_bytes;
+} gee_server_stats;
+
+/* cfg may be NULL (defaults).  Uses the current CUDA device. */
+GEE_API gee_status gee_server_create(const gee_server_config *cfg,
+                                     gee_server **out);
+/* Builds a resident graph from a host edge list (synchronous); fails with
+ * GEE_ERR_OOM if its estimated size does not fit in the budget. */
+GEE_API gee_status gee_server_add_graph(gee_server *srv, const int32_t *edges_h,
+                                        const float *weights_h, int64_t s,
+                                        int64_t n, int64_t *graph_id);
+/* Releases a resident graph; GEE_ERR_INVALID_ARG while requests use it. */
+GEE_API gee_status gee_server_drop_graph(gee_server *srv, int64_t graph_id);
+/* Queues a request (argument errors are returned here); *ticket identifies
+ * it for gee_server_wait.  A request larger than the whole budget completes
+ * with GEE_ERR_OOM. */
+GEE_API gee_status gee_server_submit(gee_server *srv, const gee_request *req,
+                                     int64_t *ticket);
+/* Blocks until the request is done; returns its status and, if latency_ms
+ * is not NULL, the time from submission to completion.  Each ticket can be
+ * waited for once. */
+GEE_API gee_status gee_server_wait(gee_server *srv, int64_t ticket,
+                                   double *latency_ms);
+GEE_API gee_status gee_server_get_stats(gee_server *srv,
+                                        gee_server_stats *out);
+/* Finishes every queued request, then releases the server and its graphs. */
+GEE_API void gee_server_destroy(gee_server *srv);
 
 /*
  * Allocation-free edge-list embedding.  The paper has no counterpart: this

@@ -15,13 +15,15 @@ from __future__ import annotations
 
 import ctypes
 
+from . import _lib as _lib_mod
 from ._lib import (GeeError, HUB_DEGREE, MAX_CLASSES, NOALLOC_MAX_NODES, STATUS, STATUS_NAMES,
                    STRATEGIES, STRATEGY_NAMES, KernelTime, check, lib, options)
 
 __all__ = ["GeeError", "Graph", "embed", "embed_host", "histogram",
            "pick_strategy", "workspace_bytes", "status_string", "STATUS",
            "STRATEGIES", "MAX_CLASSES", "HUB_DEGREE", "load", "profile_enable",
-           "profile_read", "embed_noalloc", "NOALLOC_MAX_NODES"]
+           "profile_read", "embed_noalloc", "NOALLOC_MAX_NODES", "embed_batch",
+           "Server"]
 
 
 def load():
@@ -123,6 +125,44 @@ def embed(edges, Y, K: int, weights=None, laplacian: bool = False, *,
         _stream_handle(stream))
     check(rc, "gee_embed")
     return out
+
+
+def embed_batch(problems, *, validate_edges: bool = True, stream=None,
+                raise_on_error: bool = True):
+    """gee_embed_batch: many independent problems in one launch sequence.
+
+    ``problems``: sequence of dicts with keys ``edges`` (int32 (s, 2) CUDA
+    tensor), ``Y`` (int32 (n,)), ``K`` and optionally ``weights`` (float32
+    (s,)) and ``out`` (float32 (n, K)).  Returns the list of Z tensors, or
+    (Zs, statuses) with ``raise_on_error=False``."""
+    torch = _torch()
+    arr = (_lib_mod.Problem * max(len(problems), 1))()
+    outs = []
+    for i, q in enumerate(problems):
+        edges, Y, K = q["edges"], q["Y"], int(q["K"])
+        s = _edges_shape(edges)
+        n = Y.numel()
+        out = q.get("out")
+        if out is None:
+            out = torch.empty((n, K), dtype=torch.float32, device=Y.device)
+        outs.append(out)
+        arr[i].edges = _dev_ptr(edges, torch.int32, "edges")
+        arr[i].weights = _dev_ptr(q.get("weights"), torch.float32, "weights", (s,))
+        arr[i].s = s
+        arr[i].Y = _dev_ptr(Y, torch.int32, "Y", (n,))
+        arr[i].n = n
+        arr[i].K = K
+        arr[i].reserved = 0
+        arr[i].Z = _dev_ptr(out, torch.float32, "out", (n, K))
+    statuses = (ctypes.c_int * max(len(problems), 1))()
+    o = options(validate_edges=validate_edges)
+    rc = lib().gee_embed_batch(arr, len(problems), statuses, ctypes.byref(o),
+                               _stream_handle(stream))
+    codes = [int(statuses[i]) for i in range(len(problems))]
+    if raise_on_error:
+        check(rc, "gee_embed_batch")
+        return outs
+    return outs, codes
 
 
 def embed_noalloc(edges, Y, K: int, weights=None, *, out=None, stream=None):
@@ -281,3 +321,114 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """A gee_server: embedding requests with continuous batching.
+
+    Host arrays (numpy, or numpy views of pinned CPU tensors, which let the
+    server overlap copies with other requests' kernels) are referenced until
+    ``wait`` returns for their ticket."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, streams: int = 0, max_batch: int = 0,
+                 max_batch_edges: int = 0):
+        cfg = _lib_mod.ServerConfig()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.streams = int(streams)
+        cfg.max_batch = int(max_batch)
+        cfg.max_batch_edges = int(max_batch_edges)
+        h = ctypes.c_void_p()
+        check(lib().gee_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gee_server_create")
+        self._h = h
+        self._live = {}      # ticket -> (arrays kept alive, Z)
+        self._graph_n = {}
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("server is closed")
+        return self._h
+
+    def add_graph(self, edges, n: int, weights=None) -> int:
+        import numpy as np
+        edges = _host_buf(edges)
+        weights = _host_buf(weights)
+        s = edges.shape[0] if edges.size else 0
+        gid = ctypes.c_int64()
+        check(lib().gee_server_add_graph(
+            self.handle, _host_ptr(edges, np.int32, "edges", (s, 2)),
+            _host_ptr(weights, np.float32, "weights", (s,)), s, int(n), ctypes.byref(gid)),
+            "gee_server_add_graph")
+        self._graph_n[gid.value] = int(n)
+        return gid.value
+
+    def drop_graph(self, graph_id: int) -> None:
+        check(lib().gee_server_drop_graph(self.handle, int(graph_id)), "gee_server_drop_graph")
+        self._graph_n.pop(int(graph_id), None)
+
+    def submit(self, Y, K: int, *, graph=None, edges=None, weights=None,
+               laplacian: bool = False, out=None) -> int:
+        """Queue one request: a resident graph id (``graph``) or a host edge
+        list (``edges`` int32 (s, 2), ``weights``), with labels ``Y``.
+        Returns the ticket; ``out`` (float32 (n, K)) receives Z."""
+        import numpy as np
+        Y = _host_buf(Y)
+        n = Y.shape[0]
+        if out is None:
+            out = np.empty((n, int(K)), dtype=np.float32)
+        outv = _host_buf(out)
+        r = _lib_mod.Request()
+        r.graph = -1 if graph is None else int(graph)
+        keep = [Y, out, outv]
+        if graph is None:
+            edges = _host_buf(edges)
+            weights = _host_buf(weights)
+            s = edges.shape[0] if edges.size else 0
+            r.edges_h = _host_ptr(edges, np.int32, "edges", (s, 2))
+            r.weights_h = _host_ptr(weights, np.float32, "weights", (s,))
+            r.s = s
+            keep += [edges, weights]
+        r.n = n
+        r.Y_h = _host_ptr(Y, np.int32, "Y", (n,))
+        r.K = int(K)
+        r.laplacian = int(bool(laplacian))
+        r.Z_h = _host_ptr(outv, np.float32, "out", (n, int(K)))
+        t = ctypes.c_int64()
+        check(lib().gee_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)),
+              "gee_server_submit")
+        self._live[t.value] = (keep, out)
+        return t.value
+
+    def wait(self, ticket: int, raise_on_error: bool = True):
+        """Blocks until the request is done: (Z, latency_ms), or with
+        ``raise_on_error=False`` (Z, latency_ms, status name)."""
+        lat = ctypes.c_double()
+        rc = lib().gee_server_wait(self.handle, int(ticket), ctypes.byref(lat))
+        _, out = self._live.pop(int(ticket), (None, None))
+        if raise_on_error:
+            check(rc, "gee_server_wait")
+            return out, lat.value
+        return out, lat.value, STATUS_NAMES.get(rc, str(rc))
+
+    def stats(self) -> dict:
+        st = _lib_mod.ServerStats()
+        check(lib().gee_server_get_stats(self.handle, ctypes.byref(st)), "gee_server_get_stats")
+        return {name: int(getattr(st, name)) for name, _ in st._fields_}
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            lib().gee_server_destroy(self._h)
+        self._h = None
+        self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -59,6 +59,51 @@ class KernelTime(ctypes.Structure):
     ]
 
 
+class Problem(ctypes.Structure):
+    """gee_problem: one problem of gee_embed_batch."""
+    _fields_ = [
+        ("edges", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p),
+        ("s", ctypes.c_int64),
+        ("Y", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("K", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("Z", ctypes.c_void_p),
+    ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_int64),
+        ("streams", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("max_batch_edges", ctypes.c_int64),
+        ("reserved", ctypes.c_int64 * 2),
+    ]
+
+
+class Request(ctypes.Structure):
+    """gee_request: one request to a gee_server."""
+    _fields_ = [
+        ("graph", ctypes.c_int64),
+        ("edges_h", ctypes.c_void_p),
+        ("weights_h", ctypes.c_void_p),
+        ("s", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("Y_h", ctypes.c_void_p),
+        ("K", ctypes.c_int32),
+        ("laplacian", ctypes.c_int32),
+        ("Z_h", ctypes.c_void_p),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "submitted", "completed", "failed", "groups", "batched_requests", "max_group",
+        "max_concurrent", "resident_bytes", "peak_inflight_bytes")]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -82,6 +127,15 @@ SIGNATURES = {
     "gee_pick_strategy": (ctypes.c_int, [_I64, _I64, _I32, _OPT]),
     "gee_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I32, _I32, _I32, _OPT]),
     "gee_embed_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
+    "gee_embed_batch": (ctypes.c_int, [ctypes.POINTER(Problem), _I32,
+                                       ctypes.POINTER(ctypes.c_int), _OPT, _P]),
+    "gee_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    "gee_server_add_graph": (ctypes.c_int, [_P, _P, _P, _I64, _I64, ctypes.POINTER(_I64)]),
+    "gee_server_drop_graph": (ctypes.c_int, [_P, _I64]),
+    "gee_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]),
+    "gee_server_wait": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_double)]),
+    "gee_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "gee_server_destroy": (None, [_P]),
     "gee_profile_enable": (None, [_I32]),
     "gee_profile_read": (_I32, [ctypes.POINTER(KernelTime), _I32]),
 }

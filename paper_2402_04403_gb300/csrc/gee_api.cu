@@ -16,6 +16,8 @@ int g_sms[kMaxDevices];
 cudaMemPool_t g_pool[kMaxDevices];
 bool g_pool_ready[kMaxDevices];
 
+}  // namespace
+
 gee_status from_cuda(cudaError_t e)
 {
     if (e == cudaSuccess)
@@ -59,38 +61,7 @@ cudaError_t device_pool(cudaMemPool_t *out)
     return cudaSuccess;
 }
 
-// Scratch of one call: stream-ordered allocations released (to the pool) on
-// the same stream when the call returns.
-class Workspace : public Allocator {
-  public:
-    explicit Workspace(cudaStream_t s) : stream_(s) {}
-    ~Workspace() override
-    {
-        for (void *p : ptrs_)
-            cudaFreeAsync(p, stream_);
-    }
-    cudaError_t alloc(void **p, size_t bytes) override
-    {
-        if (!pool_) {
-            cudaError_t e = device_pool(&pool_);
-            if (e != cudaSuccess)
-                return e;
-        }
-        if (bytes == 0)
-            bytes = 16;
-        // round up so vector accesses past the logical end stay inside
-        bytes = (bytes + 255) & ~size_t(255);
-        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool_, stream_);
-        if (e == cudaSuccess)
-            ptrs_.push_back(*p);
-        return e;
-    }
-
-  private:
-    cudaStream_t stream_;
-    cudaMemPool_t pool_ = nullptr;
-    std::vector<void *> ptrs_;
-};
+namespace {
 
 // Long-lived arrays of a resident graph.
 class GraphAllocator : public Allocator {
@@ -144,6 +115,12 @@ gee_status check_common(int64_t s, int64_t n, int32_t K, int32_t threads)
     if (threads != 0 && (threads % 32 != 0 || threads < 32 || threads > 1024))
         return GEE_ERR_INVALID_ARG;
     return GEE_OK;
+}
+
+// Edge lists are read one int2 per edge.
+inline bool edges_misaligned(const int32_t *E)
+{
+    return (reinterpret_cast<uintptr_t>(E) & 7) != 0;
 }
 
 #define GEE_CHECK_CUDA(x)                                                      \
@@ -393,9 +370,12 @@ gee_status ensure_laplacian(gee_graph *g, cudaStream_t stream)
     return GEE_OK;
 }
 
-gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
-                           int32_t K, int32_t laplacian, float *Z,
-                           cudaStream_t stream, int32_t L = 1)
+}  // namespace
+
+gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
+                                   const int32_t *Y, int32_t L, int32_t K,
+                                   int32_t laplacian, float *Z,
+                                   DevStatus **st_out, cudaStream_t stream)
 {
     if (laplacian) {
         gee_status rc = ensure_laplacian(graph, stream);
@@ -420,8 +400,20 @@ gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
     }
     if (rc != GEE_OK)
         return rc;
-    rc = pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
-                   stream, L);
+    *st_out = st;
+    return pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
+                     stream, L);
+}
+
+namespace {
+
+gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
+                           int32_t K, int32_t laplacian, float *Z,
+                           cudaStream_t stream, int32_t L = 1)
+{
+    DevStatus *st = nullptr;
+    gee_status rc =
+        graph_pass_enqueue(ws, graph, Y, L, K, laplacian, Z, &st, stream);
     if (rc != GEE_OK)
         return rc;
     return read_status(st, stream);
@@ -532,6 +524,8 @@ gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
         return rc;
     if ((s > 0 && edges == nullptr) || (n > 0 && (Y == nullptr || Z == nullptr)))
         return GEE_ERR_INVALID_ARG;
+    if (edges_misaligned(edges))
+        return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
     if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
@@ -604,6 +598,82 @@ void gee_graph_destroy(gee_graph *graph)
     delete graph;
 }
 
+gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
+                           gee_status *statuses, const gee_options *opts,
+                           gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (count < 0 || (count > 0 && problems == nullptr))
+        return GEE_ERR_INVALID_ARG;
+    const gee_options o = resolve_options(opts);
+    std::vector<BatchProblem> P((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        const gee_problem &q = problems[i];
+        gee_status rc = check_common(q.s, q.n, q.K, 0);
+        if (rc == GEE_OK &&
+            ((q.s > 0 && q.edges == nullptr) ||
+             (q.n > 0 && (q.Y == nullptr || q.Z == nullptr)) ||
+             edges_misaligned(q.edges) || q.reserved != 0))
+            rc = GEE_ERR_INVALID_ARG;
+        if (rc == GEE_OK && q.s > 0 && q.n == 0)
+            rc = GEE_ERR_NODE_RANGE;
+        if (rc != GEE_OK) {
+            if (statuses != nullptr)
+                statuses[i] = rc;
+            return rc;
+        }
+        BatchProblem &p = P[(size_t)i];
+        p = BatchProblem{};
+        p.E = q.edges;
+        p.w = q.weights;
+        p.Y = q.Y;
+        p.Z = q.Z;
+        p.s = q.s;
+        p.n = q.n;
+        p.K = q.K;
+    }
+    if (count == 0)
+        return GEE_OK;
+    BatchHeader hh{};
+    batch_layout(P.data(), count, hh);
+    Workspace ws(stream);
+    BatchHeader *dh = nullptr;
+    BatchProblem *dP = nullptr;
+    DevStatus *st = nullptr;
+    uint32_t *counts = nullptr;
+    uint8_t *Yc = nullptr;
+    GEE_CHECK_CUDA(ws.alloc((void **)&dh, sizeof(BatchHeader)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&dP, sizeof(BatchProblem) * count));
+    GEE_CHECK_CUDA(ws.alloc((void **)&st, sizeof(DevStatus) * count));
+    GEE_CHECK_CUDA(ws.alloc((void **)&counts, sizeof(uint32_t) * hh.count_cells));
+    GEE_CHECK_CUDA(ws.alloc((void **)&Yc, (size_t)hh.yc_bytes + 16));
+    for (int32_t i = 0; i < count; ++i) {
+        BatchProblem &p = P[(size_t)i];
+        p.st = st + i;
+        p.counts = counts + p.counts_off;
+        p.Yc = Yc + p.yc_off;
+    }
+    hh.counts = counts;
+    GEE_CHECK_CUDA(cudaMemcpyAsync(dh, &hh, sizeof(hh), cudaMemcpyHostToDevice,
+                                   stream));
+    GEE_CHECK_CUDA(cudaMemcpyAsync(dP, P.data(), sizeof(BatchProblem) * count,
+                                   cudaMemcpyHostToDevice, stream));
+    GEE_CHECK_CUDA(batch_enqueue(dh, dP, hh, o.validate_edges != 0, stream));
+    std::vector<DevStatus> hs((size_t)count);
+    GEE_CHECK_CUDA(cudaMemcpyAsync(hs.data(), st, sizeof(DevStatus) * count,
+                                   cudaMemcpyDeviceToHost, stream));
+    GEE_CHECK_CUDA(cudaStreamSynchronize(stream));
+    gee_status first = GEE_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        const gee_status r = static_cast<gee_status>(hs[(size_t)i].code);
+        if (statuses != nullptr)
+            statuses[i] = r;
+        if (first == GEE_OK)
+            first = r;
+    }
+    return first;
+}
+
 gee_status gee_graph_create(const int32_t *edges, const float *weights,
                             int64_t s, int64_t n, gee_stream_t stream_,
                             gee_graph **out)
@@ -615,7 +685,7 @@ gee_status gee_graph_create(const int32_t *edges, const float *weights,
     gee_status rc = check_common(s, n, 1, 0);
     if (rc != GEE_OK)
         return rc;
-    if (s > 0 && edges == nullptr)
+    if ((s > 0 && edges == nullptr) || edges_misaligned(edges))
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "gee.h"
 
 namespace gee {
@@ -190,6 +192,49 @@ struct Allocator {
     virtual ~Allocator() {}
 };
 
+gee_status from_cuda(cudaError_t e);
+
+// The library's stream-ordered pool on the current device.  Freed blocks stay
+// cached in the pool (release threshold = max) so repeated calls do not go
+// back to the driver.
+cudaError_t device_pool(cudaMemPool_t *out);
+
+// Scratch of one call: stream-ordered allocations, released (to the pool) on
+// the same stream when the Workspace is destroyed -- after the work enqueued
+// before, so a Workspace may go out of scope as soon as its work is queued.
+class Workspace : public Allocator {
+  public:
+    explicit Workspace(cudaStream_t s) : stream_(s) {}
+    ~Workspace() override
+    {
+        for (void *p : ptrs_)
+            cudaFreeAsync(p, stream_);
+    }
+    Workspace(const Workspace &) = delete;
+    Workspace &operator=(const Workspace &) = delete;
+    cudaError_t alloc(void **p, size_t bytes) override
+    {
+        if (!pool_) {
+            cudaError_t e = device_pool(&pool_);
+            if (e != cudaSuccess)
+                return e;
+        }
+        if (bytes == 0)
+            bytes = 16;
+        // round up so vector accesses past the logical end stay inside
+        bytes = (bytes + 255) & ~size_t(255);
+        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool_, stream_);
+        if (e == cudaSuccess)
+            ptrs_.push_back(*p);
+        return e;
+    }
+
+  private:
+    cudaStream_t stream_;
+    cudaMemPool_t pool_ = nullptr;
+    std::vector<void *> ptrs_;
+};
+
 // Builds the symmetric CSR of an edge list (validating endpoints into st).
 // `persist` provides the arrays kept in g, `tmp` the scratch.  Synchronises
 // the stream (twice) to size the arrays.
@@ -244,6 +289,60 @@ cudaError_t launch_wide_chunks(const Csr &g, int32_t L, int32_t K,
                                const uint8_t *Yc, const uint32_t *counts,
                                float *Z, void *hub_part, const DevStatus *st,
                                cudaStream_t stream);
+
+// ------------------------------------------------------------ batches
+// Many independent edge-list problems in one launch sequence (gee_batch.cu).
+// Work is cut into per-warp chunks of each kind; every problem's chunks are
+// numbered consecutively in problem order.
+constexpr int64_t kBatchNodeChunk = 4096;
+constexpr int64_t kBatchEdgeChunk = 4096;
+constexpr int64_t kBatchCellChunk = 16384;
+enum { kChunkNodes = 0, kChunkEdges = 1, kChunkCells = 2 };
+enum { kWorkLabels = 0, kWorkValidate, kWorkZero, kWorkScatter, kWorkFinalize,
+       kWorkCounters };
+
+// One problem as the kernels see it (device copy of the table).
+struct BatchProblem {
+    const int32_t *E;       // int32 [s][2]
+    const float *w;         // [s] or null (unit weights)
+    const int32_t *Y;       // [n]
+    float *Z;               // [n][K]
+    int64_t s, n;
+    int32_t K, pad;
+    uint32_t *counts;       // [K] class sizes (scratch)
+    uint8_t *Yc;            // [n] compact labels (scratch)
+    DevStatus *st;          // this problem's status (scratch)
+    int64_t node_chunk0, edge_chunk0, cell_chunk0;  // first chunk of each kind
+    int64_t counts_off, yc_off;  // scratch layout (host side)
+};
+
+struct BatchHeader {
+    int64_t count;          // problems
+    int64_t count_cells;    // total K over problems (the counts array)
+    int64_t node_chunks, edge_chunks, cell_chunks;
+    int64_t yc_bytes;
+    uint32_t *counts;
+    unsigned long long work[kWorkCounters];  // chunk counters, reset by init
+};
+
+// Host: numbers the chunks of every problem and lays out the scratch
+// (counts_off, yc_off); fills the header's sizes.  Returns yc_bytes.
+int64_t batch_layout(BatchProblem *P, int count, BatchHeader &h);
+// Enqueues the phases (init, labels, [validate,] zero, scatter, finalize)
+// for a header and problem table already in device memory; hh is the host
+// copy of the header (for sizing the init grid).
+cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
+                          const BatchHeader &hh, bool validate,
+                          cudaStream_t stream);
+
+// ------------------------------------------------------------ runtime
+// S1-S5 of L label vectors (Y[l*n + i], L >= 1) on a resident graph,
+// enqueued on `stream` without waiting: *st receives the call's device
+// status word (in ws).  Z is [n][L*K].  Argument checks are the caller's.
+gee_status graph_pass_enqueue(Workspace &ws, gee_graph *graph,
+                              const int32_t *Y, int32_t L, int32_t K,
+                              int32_t laplacian, float *Z, DevStatus **st,
+                              cudaStream_t stream);
 
 // ------------------------------------------------------------ tracing
 // When tracing is on (gee_profile_enable), a ProfScope brackets one kernel

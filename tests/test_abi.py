@@ -82,3 +82,67 @@ def test_argument_checks_return_before_any_device_work(gee):
     lib.gee_graph_destroy(null)  # no-op
     o = gee._lib.options(block=48)
     assert lib.gee_embed(null, null, 0, null, 0, 2, 0, null, ctypes.byref(o), null) == 1
+
+
+def test_batch_argument_checks_need_no_gpu(gee):
+    """gee_embed_batch rejects bad arguments on the host, before any CUDA call."""
+    from paper_2402_04403_gb300 import _lib
+    lib = gee.load()
+    name = lambda rc: gee.STATUS_NAMES[rc]
+    assert name(lib.gee_embed_batch(None, -1, None, None, None)) == "GEE_ERR_INVALID_ARG"
+    arr = (_lib.Problem * 2)()
+    st = (ctypes.c_int * 2)()
+    for i in range(2):
+        arr[i].K, arr[i].n, arr[i].s = 3, 0, 0
+    arr[1].K = 256
+    assert name(lib.gee_embed_batch(arr, 2, st, None, None)) == "GEE_ERR_UNSUPPORTED"
+    assert name(st[1]) == "GEE_ERR_UNSUPPORTED"
+    arr[1].K, arr[1].reserved = 3, 1
+    assert name(lib.gee_embed_batch(arr, 2, st, None, None)) == "GEE_ERR_INVALID_ARG"
+    arr[1].reserved = 0
+    arr[1].s, arr[1].n, arr[1].edges = 4, 10, 4     # 4-byte aligned edge pointer
+    arr[1].Y = arr[1].Z = 256
+    assert name(lib.gee_embed_batch(arr, 2, st, None, None)) == "GEE_ERR_INVALID_ARG"
+    arr[1].edges, arr[1].n = 256, 0                   # edges but no nodes
+    assert name(lib.gee_embed_batch(arr, 2, st, None, None)) == "GEE_ERR_NODE_RANGE"
+
+
+def test_misaligned_edge_lists_are_rejected(gee):
+    """Edge lists are read one 8-byte pair at a time; a 4-byte aligned
+    pointer is refused before anything runs."""
+    lib = gee.load()
+    rc = lib.gee_embed(ctypes.c_void_p(4), None, 1, ctypes.c_void_p(256), 2, 2, 0,
+                       ctypes.c_void_p(256), None, None)
+    assert gee.STATUS_NAMES[rc] == "GEE_ERR_INVALID_ARG"
+    g = ctypes.c_void_p()
+    rc = lib.gee_graph_create(ctypes.c_void_p(4), None, 1, 2, None, ctypes.byref(g))
+    assert gee.STATUS_NAMES[rc] == "GEE_ERR_INVALID_ARG"
+    rc = lib.gee_embed_noalloc(ctypes.c_void_p(12), None, 1, ctypes.c_void_p(256), 2, 2,
+                               ctypes.c_void_p(256), None)
+    assert gee.STATUS_NAMES[rc] == "GEE_ERR_INVALID_ARG"
+
+
+def test_server_argument_checks_need_no_gpu(gee):
+    """The server entry points check their arguments on the host; without a
+    CUDA device, creating a server fails with a status instead of crashing."""
+    import torch
+    from paper_2402_04403_gb300 import _lib
+    lib = gee.load()
+    name = lambda rc: gee.STATUS_NAMES[rc]
+    h = ctypes.c_void_p()
+    assert name(lib.gee_server_create(None, None)) == "GEE_ERR_INVALID_ARG"
+    cfg = _lib.ServerConfig()
+    cfg.streams = 17
+    assert name(lib.gee_server_create(ctypes.byref(cfg), ctypes.byref(h))) == "GEE_ERR_INVALID_ARG"
+    cfg.streams, cfg.reserved[0] = 0, 1
+    assert name(lib.gee_server_create(ctypes.byref(cfg), ctypes.byref(h))) == "GEE_ERR_INVALID_ARG"
+    r = _lib.Request()
+    t = ctypes.c_int64()
+    assert name(lib.gee_server_submit(None, ctypes.byref(r), ctypes.byref(t))) == \
+        "GEE_ERR_INVALID_ARG"
+    assert name(lib.gee_server_wait(None, 1, None)) == "GEE_ERR_INVALID_ARG"
+    assert name(lib.gee_server_drop_graph(None, 0)) == "GEE_ERR_INVALID_ARG"
+    lib.gee_server_destroy(None)
+    if not torch.cuda.is_available():
+        rc = lib.gee_server_create(None, ctypes.byref(h))
+        assert rc != 0 and not h.value

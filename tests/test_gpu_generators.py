@@ -32,3 +32,14 @@ def test_labels_and_weights_device_match_host(torch):
     h = graphgen.weights(50000, seed=10, start=5)
     d = graphgen.weights_device(50000, seed=10, start=5)
     assert np.array_equal(h, d.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,K", [(1000, 1), (12345, 7), (100_000, 32), (2_000_000_000, 3)])
+def test_planted_partition_device_matches_host(torch, n, K):
+    for start in (0, 987_654_321):
+        h = graphgen.planted_edges(n, K, 20000, 10.0, seed=11, start=start)
+        d = graphgen.planted_edges_device(n, K, 20000, 10.0, seed=11, start=start)
+        assert np.array_equal(h, d.cpu().numpy())
+    if n <= 100_000:
+        assert np.array_equal(graphgen.planted_labels(n, K),
+                              graphgen.planted_labels_device(n, K).cpu().numpy())

@@ -1,0 +1,198 @@
+"""The serving runtime (gee_server_*) through the C ABI: requests submitted
+in a burst or from several client threads are batched and overlapped, and
+every result is the same as that request's solo call (bit for bit with
+unit weights, 1e-5 relative with float weights); admission respects the
+memory budget; a failing request does not disturb the others."""
+import threading
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gee():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_04403_gb300 as gee
+    gee.load()
+    return gee
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _close(got, want, what):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    nz = want != 0
+    assert np.all(got[~nz] == 0), what
+    if nz.any():
+        rel = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+        assert rel.max() <= REL_TOL, f"{what}: {rel.max():.3e}"
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    """Two graphs to keep resident: weighted R-MAT with multi-chunk hub rows,
+    unweighted planted partition."""
+    nA, sA = 20000, 300000
+    eA = graphgen.rmat_edges(15, nA, 0, sA, seed=71)
+    wA = graphgen.weights(sA, seed=72)
+    nB, sB = 30000, 200000
+    eB = graphgen.planted_edges(nB, 6, sB, 10.0, seed=73)
+    return (eA, wA, nA), (eB, None, nB)
+
+
+def _edge_requests(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(50, 20000))
+        K = int(rng.integers(2, 40))
+        s = int(n * rng.uniform(1, 20))
+        e = graphgen.planted_edges(n, min(K, n), s, 10.0, seed=seed * 100 + i)
+        Y = graphgen.labels(n, K, seed=seed * 100 + i, frac_unlabeled=0.1)
+        w = graphgen.weights(s, seed=seed * 100 + i) if i % 2 else None
+        out.append((e, w, Y, K))
+    return out
+
+
+def test_mixed_burst_equals_solo_calls(gee, graphs):
+    (eA, wA, nA), (eB, _, nB) = graphs
+    with gee.Server(streams=4, max_batch=64) as srv:
+        gA = srv.add_graph(eA, nA, weights=wA)
+        gB = srv.add_graph(eB, nB)
+        reqs = []
+        for e, w, Y, K in _edge_requests(24, seed=1):
+            reqs.append(("edges", (e, w, Y, K), srv.submit(Y, K, edges=e, weights=w)))
+        for l in range(12):   # same graph and K: one multi-label group (wide form)
+            Y = graphgen.labels(nB, 9, seed=500 + l, frac_unlabeled=0.05)
+            reqs.append(("B", (Y, 9, False), srv.submit(Y, 9, graph=gB)))
+        for l in range(3):    # a small group of weighted re-labelings
+            Y = graphgen.labels(nA, 5, seed=600 + l, frac_unlabeled=0.1)
+            reqs.append(("A", (Y, 5, False), srv.submit(Y, 5, graph=gA)))
+        Y = graphgen.labels(nA, 7, seed=700)
+        reqs.append(("A", (Y, 7, True), srv.submit(Y, 7, graph=gA, laplacian=True)))
+        results = [(kind, args, srv.wait(t)) for kind, args, t in reqs]
+        st = srv.stats()
+    assert st["completed"] == st["submitted"] == len(reqs) and st["failed"] == 0
+    assert st["groups"] < len(reqs) and st["max_group"] >= 12
+    with gee.Graph(_dev(eA), nA, weights=_dev(wA)) as GA, gee.Graph(_dev(eB), nB) as GB:
+        for kind, args, (Z, lat) in results:
+            assert lat > 0
+            if kind == "edges":
+                e, w, Y, K = args
+                if w is None:
+                    assert np.array_equal(Z, oracle.embed_counts32(e, Y, K))
+                else:
+                    solo = gee.embed(_dev(e), _dev(Y), K, weights=_dev(w)).cpu().numpy()
+                    _close(Z, solo, "edge-list request")
+            else:
+                Y, K, lap = args
+                g = GA if kind == "A" else GB
+                solo = g.embed(_dev(Y), K, laplacian=lap).cpu().numpy()
+                if kind == "B":
+                    assert np.array_equal(Z, solo)
+                else:
+                    _close(Z, solo, f"re-label {kind} lap={lap}")
+    # spot checks against the oracle itself
+    Y, K, _ = results[24][1]
+    assert np.array_equal(results[24][2][0], oracle.embed_counts32(eB, Y, K))
+
+
+def test_concurrent_clients(gee, graphs):
+    (eB, _, nB) = graphs[1]
+    errors = []
+    with gee.Server(streams=3, max_batch=16) as srv:
+        gB = srv.add_graph(eB, nB)
+
+        def client(cid):
+            rng = np.random.default_rng(cid)
+            try:
+                for j in range(12):
+                    if j % 3 == 0:
+                        Y = graphgen.labels(nB, 4, seed=cid * 1000 + j)
+                        Z, _ = srv.wait(srv.submit(Y, 4, graph=gB))
+                        want = oracle.embed_counts32(eB, Y, 4)
+                    else:
+                        n = int(rng.integers(10, 3000))
+                        e = graphgen.random_graph(n, 4 * n, seed=cid * 1000 + j)
+                        Y = graphgen.labels(n, 6, seed=cid * 1000 + j, frac_unlabeled=0.2)
+                        Z, _ = srv.wait(srv.submit(Y, 6, edges=e))
+                        want = oracle.embed_counts32(e, Y, 6)
+                    if not np.array_equal(Z, want):
+                        errors.append((cid, j))
+            except Exception as exc:  # reported below
+                errors.append((cid, repr(exc)))
+
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(timeout=300)
+        assert srv.stats()["completed"] == 48
+    assert not errors, errors
+
+
+def test_admission_by_budget(gee):
+    """With a budget that holds about one request at a time everything still
+    completes, in-flight bytes stay under the budget, and a request larger
+    than the whole budget fails with GEE_ERR_OOM."""
+    reqs = _edge_requests(10, seed=3)
+    biggest = max(e.shape[0] * 12 + Y.size * (8 + 4 * K) for e, w, Y, K in reqs)
+    budget = 2 * biggest + (1 << 20)
+    with gee.Server(hbm_budget_bytes=budget, streams=4) as srv:
+        tickets = [srv.submit(Y, K, edges=e, weights=w) for e, w, Y, K in reqs]
+        n = 200_000
+        e = graphgen.random_graph(n, budget // 8, seed=9)
+        Y = graphgen.labels(n, 3, seed=9)
+        big = srv.submit(Y, 3, edges=e)
+        for (e_, w, Y_, K), t in zip(reqs, tickets):
+            Z, _ = srv.wait(t)
+            if w is None:
+                assert np.array_equal(Z, oracle.embed_counts32(e_, Y_, K))
+        _, _, status = srv.wait(big, raise_on_error=False)
+        assert status == "GEE_ERR_OOM"
+        st = srv.stats()
+        assert 0 < st["peak_inflight_bytes"] <= budget
+
+
+def test_bad_label_fails_only_its_request(gee, graphs):
+    (eB, _, nB) = graphs[1]
+    with gee.Server(streams=1) as srv:
+        gB = srv.add_graph(eB, nB)
+        # hold the only slot so the re-labelings queue up and group
+        e = graphgen.random_graph(50000, 2_000_000, seed=1)
+        Yb = graphgen.labels(50000, 3, seed=1)
+        first = srv.submit(Yb, 3, edges=e)
+        Ys = [graphgen.labels(nB, 5, seed=800 + l) for l in range(6)]
+        Ys[3][123] = 5
+        tickets = [srv.submit(Y, 5, graph=gB) for Y in Ys]
+        srv.wait(first)
+        out = [srv.wait(t, raise_on_error=False) for t in tickets]
+        assert [o[2] for o in out] == ["GEE_OK"] * 3 + ["GEE_ERR_LABEL_RANGE"] + ["GEE_OK"] * 2
+        for l in (0, 5):
+            assert np.array_equal(out[l][0], oracle.embed_counts32(eB, Ys[l], 5))
+        # a graph with queued work cannot be dropped; afterwards it can
+        # (the edge list ahead of it keeps the re-labeling queued)
+        ahead = srv.submit(Yb, 3, edges=e)
+        t = srv.submit(Ys[0], 5, graph=gB)
+        with pytest.raises(gee.GeeError):
+            srv.drop_graph(gB)
+        srv.wait(ahead)
+        srv.wait(t)
+        srv.drop_graph(gB)
+        with pytest.raises(gee.GeeError):
+            srv.submit(Ys[0], 5, graph=gB)

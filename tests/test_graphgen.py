@@ -74,3 +74,31 @@ def test_sbm_structure(tiny_sbm_graph):
     lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
     key = lo.astype(np.int64) * 10000 + hi
     assert np.unique(key).size == key.size  # simple graph
+
+
+def test_planted_partition_structure():
+    """Blocks are floor(i K / n) (sizes differ by at most one); endpoints are
+    in range; the share of edges inside a block matches its threshold and the
+    share p_in (b-1) / (p_in (b-1) + p_out (n-b)) of an SBM node's expected
+    edges; K = 1 keeps every edge inside the single block."""
+    n, K, s = 10007, 9, 300000
+    y = graphgen.planted_labels(n, K)
+    sizes = np.bincount(y)
+    assert sizes.size == K and sizes.max() - sizes.min() <= 1
+    assert np.array_equal(graphgen.planted_block_start(np.arange(K + 1), n, K),
+                          np.concatenate([[0], np.cumsum(sizes)]))
+    e = graphgen.planted_edges(n, K, s, 10.0, seed=4)
+    assert e.min() >= 0 and e.max() < n
+    same = (y[e[:, 0]] == y[e[:, 1]]).mean()
+    b = n / K
+    q = 10 * (b - 1) / (10 * (b - 1) + n - b)
+    assert abs(same - q) < 4 * np.sqrt(q * (1 - q) / s)
+    assert abs(graphgen.planted_same_threshold(n, K, 10.0) / 2**32 - q) < 1e-9
+    # first endpoints are uniform over nodes: each block gets its share
+    frac = np.bincount(y[e[:, 0]], minlength=K) / s
+    assert np.allclose(frac, sizes / n, atol=0.01)
+    e1 = graphgen.planted_edges(500, 1, 1000, 10.0, seed=4)
+    assert e1.min() >= 0 and e1.max() < 500
+    # same seed, sliced: identical edges
+    assert np.array_equal(graphgen.planted_edges(n, K, 100, 10.0, seed=4, start=50),
+                          e[50:150])
