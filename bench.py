@@ -62,6 +62,13 @@ WORKLOADS = {
                       graphs=4096, n_lo=1e3, n_hi=1e5, deg_lo=10, deg_hi=50, K_lo=2, K_hi=32,
                       ratio=10.0, weighted=True, laplacian=False, seed=4,
                       scale=0, n=0, s=0, K=0),
+    "serve": dict(desc="serving: Poisson stream of embedding requests, graphs of 1e3-1e8 edges "
+                        "(log-uniform; R-MAT and planted partition half and half; n = s/8), K "
+                        "uniform in [2, 64], 30% re-labelings of resident graphs, 80 GiB "
+                        "admission budget, host buffers in page-locked memory",
+                  pool=64, resident=8, s_lo=1e3, s_hi=1e8, K_lo=2, K_hi=64, relabel=0.3,
+                  load=0.8, budget=80 << 30, streams=4, max_batch=256, seed=5,
+                  weighted=False, laplacian=False, scale=0, n=0, s=0, K=0),
     "rmat24lap": dict(desc="R-MAT scale 24 weighted, Laplacian variant",
                       scale=24, n=1 << 24, s=268_435_456, K=20, frac_unlabeled=0.1,
                       weighted=True, laplacian=True, seed=2),
@@ -495,6 +502,177 @@ def run_batch(args, w, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, w, world, rank, local):
+    """Serving (gee_server_*): a burst of all requests for the server's
+    throughput, then a Poisson stream at `load` x the plain path's capacity
+    for its latencies; the plain path is one synchronous host-buffer call per
+    request (gee_embed_host, or gee_embed_graph_host on a resident graph),
+    whose latencies under the same arrivals follow from its measured service
+    times (first-in first-out, one call at a time)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2402_04403_gb300 as gee
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(w["seed"])
+    P, R = w["pool"], args.requests
+    # the graph pool: edges and four label vectors per graph in pinned memory
+    pool = []
+    for g in range(P):
+        s_g = int(np.exp(rng.uniform(np.log(w["s_lo"]), np.log(w["s_hi"]))))
+        n_g = max(s_g // 8, 16)
+        if g % 2 == 0:
+            scale = max(1, int(np.ceil(np.log2(n_g))))
+            e = graphgen.rmat_edges_device(scale, n_g, 0, s_g, w["seed"] * 1000 + g, device=dev)
+        else:
+            kb = int(rng.integers(2, 65))
+            e = graphgen.planted_edges_device(n_g, min(kb, n_g), s_g, 10.0,
+                                              w["seed"] * 1000 + g, device=dev)
+        eh = torch.empty((s_g, 2), dtype=torch.int32, pin_memory=True)
+        eh.copy_(e)
+        labs = []
+        for j in range(4):
+            K = int(rng.integers(w["K_lo"], w["K_hi"] + 1))
+            yh = torch.empty(n_g, dtype=torch.int32, pin_memory=True)
+            yh.copy_(graphgen.labels_device(n_g, K, w["seed"] * 7919 + 4 * g + j, device=dev))
+            labs.append((K, yh.numpy()))
+        kmax = max(K for K, _ in labs)
+        out = torch.empty((n_g, kmax), dtype=torch.float32, pin_memory=True).numpy()
+        pool.append(dict(s=s_g, n=n_g, edges=eh.numpy(), labs=labs, out=out))
+        del e
+    torch.cuda.synchronize()
+    resident = list(range(0, P, P // w["resident"]))[: w["resident"]]
+    kinds = rng.random(R) < w["relabel"]
+    picks = [(int(rng.choice(resident)) if kinds[i] else int(rng.integers(P)),
+              int(rng.integers(4))) for i in range(R)]
+    edges_of = [pool[g]["s"] for g, _ in picks]
+    total_edges = float(sum(edges_of))
+
+    def zbuf(g, K):
+        o = pool[g]["out"]
+        return o.reshape(-1)[: pool[g]["n"] * K].reshape(pool[g]["n"], K)
+
+    # plain: one synchronous call per request, graphs kept resident on the device
+    dev_graphs = {}
+    for g in resident:
+        dev_graphs[g] = gee.Graph(torch.from_numpy(pool[g]["edges"]).to(dev), pool[g]["n"])
+    service = np.empty(R)
+    for warm in range(2):
+        g, j = picks[warm]
+        K, Y = pool[g]["labs"][j]
+        gee.embed_host(pool[g]["edges"], Y, K, out=zbuf(g, K))
+    for i, (g, j) in enumerate(picks):
+        K, Y = pool[g]["labs"][j]
+        t0 = time.perf_counter()
+        if kinds[i]:
+            dev_graphs[g].embed_host(Y, K, out=zbuf(g, K))
+        else:
+            gee.embed_host(pool[g]["edges"], Y, K, out=zbuf(g, K))
+        service[i] = time.perf_counter() - t0
+    plain_total = float(service.sum())
+    # a few results to compare with the server's (copied before they are overwritten)
+    check_ids = [i for i in range(R) if kinds[i]][:2] + [i for i in range(R) if not kinds[i]][:2]
+
+    with gee.Server(hbm_budget_bytes=w["budget"], streams=w["streams"],
+                    max_batch=w["max_batch"]) as srv:
+        gid = {g: srv.add_graph(pool[g]["edges"], pool[g]["n"]) for g in resident}
+
+        def submit(i):
+            g, j = picks[i]
+            K, Y = pool[g]["labs"][j]
+            if kinds[i]:
+                return srv.submit(Y, K, graph=gid[g], out=zbuf(g, K))
+            return srv.submit(Y, K, edges=pool[g]["edges"], out=zbuf(g, K))
+
+        # agreement with the plain path on a few requests
+        worst = 0.0
+        for i in check_ids:
+            g, j = picks[i]
+            K, Y = pool[g]["labs"][j]
+            if kinds[i]:
+                want = dev_graphs[g].embed_host(Y, K)
+            else:
+                want = gee.embed_host(pool[g]["edges"], Y, K)
+            got, _ = srv.wait(submit(i))
+            worst = max(worst, float(np.abs(got - want).max()))
+        # burst: every request at once -> throughput
+        t0 = time.perf_counter()
+        tickets = [submit(i) for i in range(R)]
+        for t in tickets:
+            srv.wait(t)
+        burst_s = time.perf_counter() - t0
+        st_burst = srv.stats()
+        # Poisson arrivals at load x the plain capacity -> latencies
+        lam = w["load"] * R / plain_total
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, R))
+        lat = np.empty(R)
+        tickets = [None] * R
+        ready = threading.Semaphore(0)
+
+        def client():
+            base = time.perf_counter()
+            for i in range(R):
+                d = base + arrivals[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = submit(i)
+                ready.release()
+
+        sampler = ClockSampler(local) if not args.no_clocks else None
+        th = threading.Thread(target=client)
+        t0 = time.perf_counter()
+        th.start()
+        for i in range(R):
+            ready.acquire()
+            _, lat[i] = srv.wait(tickets[i])
+        th.join()
+        stream_s = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        st = srv.stats()
+    for g in dev_graphs.values():
+        g.close()
+    # plain latencies under the same arrivals: FIFO, one call at a time
+    finish = 0.0
+    plain_lat = np.empty(R)
+    for i in range(R):
+        start = max(arrivals[i], finish)
+        finish = start + service[i]
+        plain_lat[i] = (finish - arrivals[i]) * 1e3
+    pct = lambda a, q: float(np.percentile(a, q))
+    line = {
+        "metric": "serving: edges/s and p50/p99 latency vs sequential plain calls",
+        "value": world * total_edges / burst_s, "unit": "edges/s", "n_gpus": world,
+        "steps": R, "warmup": 2, "ms_per_step": burst_s * 1e3 / R,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w["desc"], "name": args.workload, "requests": R,
+                   "pool_graphs": P, "resident_graphs": len(resident),
+                   "edges_total": total_edges, "budget_bytes": w["budget"],
+                   "streams": w["streams"], "max_batch": w["max_batch"],
+                   "parallelism": "replicas"},
+        "plain": {"value": total_edges / plain_total, "seconds": plain_total,
+                  "p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99),
+                  "api": "gee_embed_host / gee_embed_graph_host, one at a time"},
+        "served": {"burst_seconds": burst_s, "edges_per_s": total_edges / burst_s,
+                   "poisson_rate_per_s": lam, "load_vs_plain_capacity": w["load"],
+                   "stream_seconds": stream_s, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                   "p50_ms_plain_same_arrivals": pct(plain_lat, 50),
+                   "p99_ms_plain_same_arrivals": pct(plain_lat, 99)},
+        "speedup_vs_plain": plain_total / burst_s,
+        "max_abs_diff_vs_plain": worst,
+        "server_stats": {"burst": st_burst, "end": st},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w, world, rank, local):
     import torch
 
@@ -644,6 +822,8 @@ def main():
                     help="cpu_baseline sample = workload / 2^shift")
     ap.add_argument("--scale-shift", type=int, default=0,
                     help="shrink the workload by 2^shift (same generator; for profiling)")
+    ap.add_argument("--requests", type=int, default=10000,
+                    help="serve workload: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oneshot", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -652,7 +832,7 @@ def main():
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     w = dict(WORKLOADS[args.workload])
-    if args.scale_shift and "graphs" not in w:
+    if args.scale_shift and "graphs" not in w and "pool" not in w:
         sh = args.scale_shift
         w.update(scale=w["scale"] - sh, n=w["n"] >> sh, s=w["s"] >> sh,
                  desc=w["desc"] + f" (shrunk by 2^{sh}: n={w['n'] >> sh}, s={w['s'] >> sh})")
@@ -663,6 +843,8 @@ def main():
         run_multi(args, w, world, rank, local)
     elif "graphs" in w:
         run_batch(args, w, world, rank, local)
+    elif "pool" in w:
+        run_serve(args, w, world, rank, local)
     else:
         run_ours(args, w, world, rank, local)
     if world > 1:

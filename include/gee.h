@@ -32,6 +32,9 @@
  *     Laplacian results accumulate in float32 and are scaled once per cell.
  *   - Pointers named *_h are host memory; all others are device memory of
  *     the current CUDA device.  The caller owns every buffer it passes.
+ *     Device arrays of 4-byte elements (Y, weights, Z, counts) must be
+ *     4-byte aligned (GEE_ERR_INVALID_ARG otherwise); wider alignment is
+ *     used where present, never required.
  *   - Every call is enqueued on `stream` and returns after the stream has
  *     finished the call's work (it reads back a device status word), so the
  *     result is ready when the call returns GEE_OK.
@@ -169,7 +172,10 @@ GEE_API gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
                                          const gee_options *opts,
                                          gee_stream_t stream);
 
-/* Same with host Y_h and Z_h (e.g. pinned buffers). */
+/* Same with host Y_h and Z_h.  A page-locked Z_h (cudaMallocHost or
+ * cudaHostRegister) is written directly by the pass over the host link, so
+ * the transfer overlaps the computation; pageable Z_h is filled by a copy
+ * after the pass.  Either way Z_h is untouched when labels fail the check. */
 GEE_API gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
                                 int32_t K, int32_t laplacian, float *Z_h,
                                 const gee_options *opts, gee_stream_t stream);

@@ -123,6 +123,31 @@ inline bool edges_misaligned(const int32_t *E)
     return (reinterpret_cast<uintptr_t>(E) & 7) != 0;
 }
 
+// Y, weights, counts and Z are read and written as 4-byte words (or wider,
+// where the address allows).
+inline bool words_misaligned(const void *a, const void *b = nullptr,
+                             const void *c = nullptr)
+{
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+             reinterpret_cast<uintptr_t>(c)) & 3) != 0;
+}
+
+// Device address of page-locked (registered or cudaMallocHost) host memory,
+// or null for pageable or unaligned memory.
+float *mapped_host(float *p)
+{
+    if (p == nullptr || (reinterpret_cast<uintptr_t>(p) & 3) != 0)
+        return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory may report an error: clear it
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr)
+        return nullptr;
+    return static_cast<float *>(at.devicePointer);
+}
+
 #define GEE_CHECK_CUDA(x)                                                      \
     do {                                                                       \
         cudaError_t e_ = (x);                                                  \
@@ -493,7 +518,8 @@ gee_status gee_histogram(const int32_t *Y, int64_t n, int32_t K,
     gee_status rc = check_common(0, n, K, 0);
     if (rc != GEE_OK)
         return rc;
-    if (counts == nullptr || (n > 0 && Y == nullptr))
+    if (counts == nullptr || (n > 0 && Y == nullptr) ||
+        words_misaligned(counts, Y))
         return GEE_ERR_INVALID_ARG;
     gee_status out;
     {
@@ -524,7 +550,7 @@ gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
         return rc;
     if ((s > 0 && edges == nullptr) || (n > 0 && (Y == nullptr || Z == nullptr)))
         return GEE_ERR_INVALID_ARG;
-    if (edges_misaligned(edges))
+    if (edges_misaligned(edges) || words_misaligned(weights, Y, Z))
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
@@ -613,7 +639,8 @@ gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
         if (rc == GEE_OK &&
             ((q.s > 0 && q.edges == nullptr) ||
              (q.n > 0 && (q.Y == nullptr || q.Z == nullptr)) ||
-             edges_misaligned(q.edges) || q.reserved != 0))
+             edges_misaligned(q.edges) ||
+             words_misaligned(q.weights, q.Y, q.Z) || q.reserved != 0))
             rc = GEE_ERR_INVALID_ARG;
         if (rc == GEE_OK && q.s > 0 && q.n == 0)
             rc = GEE_ERR_NODE_RANGE;
@@ -685,7 +712,8 @@ gee_status gee_graph_create(const int32_t *edges, const float *weights,
     gee_status rc = check_common(s, n, 1, 0);
     if (rc != GEE_OK)
         return rc;
-    if ((s > 0 && edges == nullptr) || edges_misaligned(edges))
+    if ((s > 0 && edges == nullptr) || edges_misaligned(edges) ||
+        words_misaligned(weights))
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
@@ -752,7 +780,8 @@ gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
     gee_status rc = check_common(0, graph->csr.n, K, o.block);
     if (rc != GEE_OK)
         return rc;
-    if (graph->csr.n > 0 && (Y == nullptr || Z == nullptr))
+    if ((graph->csr.n > 0 && (Y == nullptr || Z == nullptr)) ||
+        words_misaligned(Y, Z))
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
     return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
@@ -772,7 +801,8 @@ gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
         return rc;
     if ((int64_t)L * K > GEE_MAX_COLUMNS)
         return GEE_ERR_UNSUPPORTED;
-    if (graph->csr.n > 0 && (Y == nullptr || Z == nullptr))
+    if ((graph->csr.n > 0 && (Y == nullptr || Z == nullptr)) ||
+        words_misaligned(Y, Z))
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
     return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, L);
@@ -794,11 +824,17 @@ gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
     int32_t *Y = nullptr;
-    float *Z = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&Y, sizeof(int32_t) * (n + 1)));
-    GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
     GEE_CHECK_CUDA(cudaMemcpyAsync(Y, Y_h, sizeof(int32_t) * n,
                                    cudaMemcpyHostToDevice, stream));
+    // A page-locked Z_h is written by the pass itself over the host link, so
+    // the transfer overlaps the pass instead of following it; labels are
+    // checked before any Z row is written, so Z_h stays untouched on error.
+    float *Zdirect = mapped_host(Z_h);
+    if (Zdirect != nullptr)
+        return embed_graph_dev(ws, graph, Y, K, laplacian, Zdirect, stream);
+    float *Z = nullptr;
+    GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
     rc = embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
     if (rc != GEE_OK)
         return rc;

@@ -765,7 +765,9 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
 
     const int64_t g0 = (int64_t)r0 * K;  // first Z cell of the tile
-    const int off = (int)(g0 & 3);       // acc[off + j] holds cell g0 + j
+    // acc[off + j] holds cell g0 + j, off = the cell's float offset within
+    // its 16-byte block of Z (any 4-byte aligned Z)
+    const int off = (int)((reinterpret_cast<uintptr_t>(a.Z + g0) >> 2) & 3);
     const int cells = NR * K;
 
     // setup: zero the accumulators, load the tile's row starts

@@ -82,7 +82,9 @@ extern "C" GEE_API gee_status gee_embed_noalloc(const int32_t *edges,
     if (K > kMaxClasses || n > (int64_t)GEE_NOALLOC_MAX_NODES)
         return GEE_ERR_UNSUPPORTED;
     if ((s > 0 && edges == nullptr) || (n > 0 && (Y == nullptr || Z == nullptr)) ||
-        (reinterpret_cast<uintptr_t>(edges) & 7) != 0)
+        (reinterpret_cast<uintptr_t>(edges) & 7) != 0 ||
+        ((reinterpret_cast<uintptr_t>(weights) | reinterpret_cast<uintptr_t>(Y) |
+          reinterpret_cast<uintptr_t>(Z)) & 3) != 0)
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;

@@ -171,6 +171,28 @@ def test_unaligned_device_pointers(gee):
     assert np.array_equal(got, want)
 
 
+def test_resident_graph_unaligned_output(gee, rmat16):
+    """A Z that starts 4, 8 or 12 bytes past a 16-byte boundary: the row
+    tiles' vector stores realign on the address, results are unchanged."""
+    import torch
+    edges, n = rmat16
+    K = 7
+    Y = graphgen.labels(n, K, seed=31, frac_unlabeled=0.1)
+    want = oracle.embed_counts32(edges, Y, K)
+    with gee.Graph(_dev(edges), n) as g:
+        for shift in (1, 2, 3):
+            buf = torch.full((n * K + 4,), 9.0, device="cuda")
+            Z = buf[shift:shift + n * K].view(n, K)
+            g.embed(_dev(Y), K, out=Z)
+            assert np.array_equal(Z.cpu().numpy(), want), shift
+            assert torch.all(buf[:shift] == 9.0) and torch.all(buf[shift + n * K:] == 9.0)
+    for shift in (1, 3):
+        buf = torch.full((n * K + 4,), 9.0, device="cuda")
+        Z = buf[shift:shift + n * K].view(n, K)
+        gee.embed(_dev(edges), _dev(Y), K, strategy="segmented", out=Z)
+        assert np.array_equal(Z.cpu().numpy(), want), shift
+
+
 def test_repeated_calls(gee, tiny_sbm_graph):
     """Unit weights: every call gives the same bits.  Float weights: the
     shared-memory float atomics may add in a different order from call to
@@ -206,6 +228,30 @@ def test_host_entry_points(gee, tiny_sbm_graph):
         assert np.array_equal(g.embed_host(Y, 5), want)
         info = g.info()
         assert info["n"] == Y.size and info["s"] == edges.shape[0]
+
+
+def test_graph_host_entry_point_writes_pinned_output_directly(gee, rmat16):
+    """gee_embed_graph_host with a page-locked Z (written by the pass itself)
+    and a pageable Z (copied after it) gives the oracle's result; on a label
+    error the page-locked Z is left untouched."""
+    import torch
+    edges, n = rmat16
+    K = 9
+    Y = graphgen.labels(n, K, seed=41, frac_unlabeled=0.1)
+    want = oracle.embed_counts32(edges, Y, K)
+    Zp = torch.full((n, K), 3.0).pin_memory()
+    Yp = torch.from_numpy(Y).pin_memory()
+    with gee.Graph(_dev(edges), n) as g:
+        g.embed_host(Yp, K, out=Zp)
+        assert np.array_equal(Zp.numpy(), want)
+        assert np.array_equal(g.embed_host(Y, K), want)           # pageable
+        bad = Y.copy()
+        bad[n // 2] = K
+        Zp.fill_(3.0)
+        with pytest.raises(gee.GeeError) as ei:
+            g.embed_host(torch.from_numpy(bad).pin_memory(), K, out=Zp)
+        assert ei.value.name == "GEE_ERR_LABEL_RANGE"
+        assert torch.all(Zp == 3.0)
 
 
 def test_relabeling_a_resident_graph(gee, rmat16):
