@@ -69,6 +69,12 @@ WORKLOADS = {
                   pool=64, resident=8, s_lo=1e3, s_hi=1e8, K_lo=2, K_hi=64, relabel=0.3,
                   load=0.8, budget=80 << 30, streams=4, max_batch=256, seed=5,
                   weighted=False, laplacian=False, scale=0, n=0, s=0, K=0),
+    "precision": dict(desc="precision ladder: each arithmetic path (uint32 counts, FP32 weight "
+                            "sums, FP32 Laplacian, multi-label and batched forms) against the "
+                            "FP64 oracle on the tiny SBM (all rows), R-MAT scale 24 and the "
+                            "paper-scale graph (sampled rows)",
+                      rows=4096, seed=6, weighted=False, laplacian=False,
+                      scale=0, n=0, s=0, K=0),
     "rmat24lap": dict(desc="R-MAT scale 24 weighted, Laplacian variant",
                       scale=24, n=1 << 24, s=268_435_456, K=20, frac_unlabeled=0.1,
                       weighted=True, laplacian=True, seed=2),
@@ -473,8 +479,13 @@ def run_batch(args, w, world, rank, local):
     gee.profile_enable(False)
     kernels = {k: {"launches": v["launches"], "ms": v["total_ms"]}
                for k, v in gee.profile_read().items()}
+    # the plain path with GEE_AUTO tuned on this device (gee_autotune)
+    tune_t0 = time.perf_counter()
+    table = gee.autotune(0)
+    tune_s = time.perf_counter() - tune_t0
     plain()  # warm-up of the plain path
     plain_ms = timed(plain, max(1, min(args.steps, 3)))
+    gee.tune_set([])
     # same results: the batch and the plain calls on every graph
     nz = Zp != 0
     worst = ((Z - Zp).abs()[nz] / Zp[nz].abs()).max().item() if nz.any() else 0.0
@@ -491,7 +502,10 @@ def run_batch(args, w, world, rank, local):
                    "api": "gee_embed_batch", "parallelism": "replicas",
                    "l2": "inputs larger than L2, no flush"},
         "plain": {"value": world * total_s / (plain_ms / 1e3), "ms": plain_ms,
-                  "api": f"{G} x gee_embed (AUTO strategy)"},
+                  "api": f"{G} x gee_embed (AUTO strategy, autotuned)",
+                  "autotune_seconds": tune_s,
+                  "autotune_choices": {k: sum(1 for c in table if c["strategy"] == k)
+                                       for k in ("atomic", "private", "segmented")}},
         "speedup_vs_plain": plain_ms / ms,
         "max_rel_diff_vs_plain": worst, "zeros_agree": zero_ok,
         "kernels_per_batch": kernels,
@@ -673,6 +687,120 @@ def run_serve(args, w, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def _errors(got, z64, zref32=None):
+    """Max abs / rel error of got against the FP64 values (rel over non-zero
+    oracle cells; cells where the oracle is 0 must be exactly 0), and the max
+    abs difference from RN32 of the exact quotient where it is known."""
+    import numpy as np
+    got = np.asarray(got, np.float64)
+    nz = z64 != 0
+    out = {"cells": int(got.size),
+           "max_abs_err_vs_fp64": float(np.abs(got - z64).max()) if got.size else 0.0,
+           "max_rel_err_vs_fp64": float((np.abs(got[nz] - z64[nz]) / np.abs(z64[nz])).max())
+           if nz.any() else 0.0,
+           "zeros_exact": bool(np.all(got[~nz] == 0))}
+    if zref32 is not None:
+        out["max_abs_diff_vs_rn32_exact"] = float(np.abs(got - zref32).max()) if got.size else 0.0
+        out["bit_exact"] = bool(np.array_equal(np.asarray(got, np.float32), zref32))
+    return out
+
+
+def run_precision(args, w, world, rank, local):
+    """The precision ladder: every arithmetic path against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import oracle
+    import paper_2402_04403_gb300 as gee
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(w["seed"])
+    report = []
+
+    def add(config, path, errs, **extra):
+        report.append(dict({"config": config, "path": path}, **errs, **extra))
+
+    # tiny SBM (the small parity workload): every row
+    e, Y = graphgen.tiny_sbm(seed=1)
+    K = 5
+    wt = graphgen.weights(e.shape[0], seed=11)
+    ed, yd, wd = (torch.from_numpy(a).to(dev) for a in (e, Y, wt))
+    z64 = oracle.embed(e, Y, K)
+    zr = oracle.embed_counts32(e, Y, K)
+    for strat in ("atomic", "private", "segmented"):
+        add("tiny SBM", f"uint32 counts ({strat})",
+            _errors(gee.embed(ed, yd, K, strategy=strat).cpu().numpy(), z64, zr))
+    z64w = oracle.embed(e, Y, K, weights=wt)
+    add("tiny SBM + weights (0,1]", "FP32 weight sums (atomic)",
+        _errors(gee.embed(ed, yd, K, weights=wd, strategy="atomic").cpu().numpy(), z64w))
+    add("tiny SBM + weights (0,1]", "FP32 weight sums (segmented)",
+        _errors(gee.embed(ed, yd, K, weights=wd, strategy="segmented").cpu().numpy(), z64w))
+    z64l = oracle.embed(e, Y, K, weights=wt, laplacian=True)
+    add("tiny SBM + weights (0,1]", "FP32 Laplacian (FP64 degree scale)",
+        _errors(gee.embed(ed, yd, K, weights=wd, laplacian=True).cpu().numpy(), z64l))
+
+    def sampled(config, edges_h, wts_h, Ys, K, graph, n, laplacian=False, multi=False):
+        """Rows: the 64 highest-degree nodes and random ones."""
+        deg = np.bincount(edges_h.ravel(), minlength=n)
+        rows = np.unique(np.concatenate([np.argsort(deg)[-64:],
+                                         rng.integers(0, n, w["rows"])]))
+        if multi:
+            Z = graph.embed_multi(torch.from_numpy(Ys).to(dev), K).cpu().numpy()
+            for l in (0, Ys.shape[0] - 1):
+                r, z64r = oracle.embed_rows(edges_h, Ys[l], K, rows, weights=wts_h)
+                add(config, f"multi-label FP32 (vector {l} of {Ys.shape[0]})",
+                    _errors(Z[r, l * K:(l + 1) * K], z64r), rows_checked=int(r.size))
+            return
+        Yd = torch.from_numpy(Ys).to(dev)
+        Z = graph.embed(Yd, K, laplacian=laplacian).cpu().numpy()
+        if wts_h is None and not laplacian:
+            r, z64r, C = oracle.embed_rows(edges_h, Ys, K, rows, with_counts=True)
+            nk = oracle.class_counts(Ys, K)
+            add(config, "uint32 counts (resident graph)",
+                _errors(Z[r], z64r, oracle.round_counts(C, nk)), rows_checked=int(r.size))
+        else:
+            r, z64r = oracle.embed_rows(edges_h, Ys, K, rows, weights=wts_h, laplacian=laplacian)
+            add(config, "FP32 Laplacian (resident graph)" if laplacian
+                else "FP32 weight sums (resident graph)",
+                _errors(Z[r], z64r), rows_checked=int(r.size))
+
+    # R-MAT scale 24 weighted (and the same graph with unit weights)
+    W = WORKLOADS["rmat24"]
+    n, s, K = W["n"], W["s"], W["K"]
+    ed = graphgen.rmat_edges_device(W["scale"], n, 0, s, W["seed"], device=dev)
+    wd = graphgen.weights_device(s, W["seed"] + 2, device=dev)
+    Yd = graphgen.labels_device(n, K, W["seed"] + 1, W["frac_unlabeled"], device=dev)
+    e_h, w_h, Y_h = ed.cpu().numpy(), wd.cpu().numpy(), Yd.cpu().numpy()
+    with gee.Graph(ed, n, weights=wd) as g:
+        sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n)
+        sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n, laplacian=True)
+        Ys = np.stack([graphgen.labels(n, K, seed=900 + l, frac_unlabeled=0.1) for l in range(32)])
+        sampled("R-MAT scale 24, weights (0,1], L=32", e_h, w_h, Ys, K, g, n, multi=True)
+    with gee.Graph(ed, n) as g:
+        sampled("R-MAT scale 24, unit weights", e_h, None, Y_h, K, g, n)
+    del ed, wd, Yd
+    torch.cuda.empty_cache()
+    # paper scale, unit weights (the headline workload)
+    W = WORKLOADS["paper"]
+    n, s, K = W["n"], W["s"], W["K"]
+    ed = graphgen.rmat_edges_device(W["scale"], n, 0, s, W["seed"], device=dev)
+    Yd = graphgen.labels_device(n, K, W["seed"] + 1, W["frac_unlabeled"], device=dev)
+    e_h, Y_h = ed.cpu().numpy(), Yd.cpu().numpy()
+    with gee.Graph(ed, n) as g:
+        del ed
+        sampled("paper scale (1.8B edges), unit weights", e_h, None, Y_h, K, g, n)
+    line = {"metric": "max error vs the FP64 oracle, per arithmetic path",
+            "value": max(r["max_rel_err_vs_fp64"] for r in report), "unit": "relative",
+            "higher_is_better": False, "n_gpus": world, "steps": 1, "warmup": 0,
+            "dtype": "u32/f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "name": args.workload}, "paths": report}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w, world, rank, local):
     import torch
 
@@ -832,7 +960,8 @@ def main():
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     w = dict(WORKLOADS[args.workload])
-    if args.scale_shift and "graphs" not in w and "pool" not in w:
+    if args.scale_shift and "graphs" not in w and "pool" not in w and \
+            args.workload != "precision":
         sh = args.scale_shift
         w.update(scale=w["scale"] - sh, n=w["n"] >> sh, s=w["s"] >> sh,
                  desc=w["desc"] + f" (shrunk by 2^{sh}: n={w['n'] >> sh}, s={w['s'] >> sh})")
@@ -845,6 +974,8 @@ def main():
         run_batch(args, w, world, rank, local)
     elif "pool" in w:
         run_serve(args, w, world, rank, local)
+    elif args.workload == "precision":
+        run_precision(args, w, world, rank, local)
     else:
         run_ours(args, w, world, rank, local)
     if world > 1:

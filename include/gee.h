@@ -200,6 +200,34 @@ GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
                            const gee_options *opts);
 
 /*
+ * Autotuning of GEE_AUTO for edge-list calls (no counterpart in the paper).
+ * gee_autotune times ATOMIC (block sizes 128, 256, 512), PRIVATE (where Z
+ * fits in shared memory) and SEGMENTED on seeded synthetic problems (K = 16,
+ * uniform random edges) over a grid of Z sizes 2^10..2^24 cells and edge
+ * densities 2s/cells = 2^-2..2^4 -- every second power of two with
+ * effort 0, every one with efforts 1 and 2 (2 also takes more repetitions)
+ * -- and installs the fastest choice per grid point for the current
+ * device; it takes seconds (effort 0) to a minute.  GEE_AUTO then uses the
+ * grid point nearest in (log2 cells, log2 density).  gee_tune_get copies
+ * the current device's table (returns its size; 0 = not tuned, the built-in
+ * rule applies); gee_tune_set installs a saved table (count 0 resets).
+ */
+typedef struct gee_tune_cell {
+    int32_t log2_cells;      /* n*K of the grid point */
+    int32_t log2_density;    /* 2s / (n*K) */
+    int32_t strategy;        /* GEE_ATOMIC, GEE_PRIVATE or GEE_SEGMENTED */
+    int32_t block;           /* threads per block (0: the default) */
+    float ms_atomic;         /* measured median call times; -1 if not run */
+    float ms_private;
+    float ms_segmented;
+    float reserved;
+} gee_tune_cell;
+
+GEE_API gee_status gee_autotune(int32_t effort, gee_stream_t stream);
+GEE_API int32_t gee_tune_get(gee_tune_cell *out, int32_t max_cells);
+GEE_API gee_status gee_tune_set(const gee_tune_cell *cells, int32_t count);
+
+/*
  * Batched embedding: `count` independent problems, each with the arguments
  * of gee_embed (its own edges, weights, Y, n, K and Z; no Laplacian), run
  * by one sequence of persistent launches over all of them -- the batched

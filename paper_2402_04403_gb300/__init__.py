@@ -23,7 +23,7 @@ __all__ = ["GeeError", "Graph", "embed", "embed_host", "histogram",
            "pick_strategy", "workspace_bytes", "status_string", "STATUS",
            "STRATEGIES", "MAX_CLASSES", "HUB_DEGREE", "load", "profile_enable",
            "profile_read", "embed_noalloc", "NOALLOC_MAX_NODES", "embed_batch",
-           "Server"]
+           "Server", "autotune", "tune_table", "tune_set"]
 
 
 def load():
@@ -163,6 +163,43 @@ def embed_batch(problems, *, validate_edges: bool = True, stream=None,
         check(rc, "gee_embed_batch")
         return outs
     return outs, codes
+
+
+def tune_table() -> list:
+    """The current device's GEE_AUTO tuning table (empty if not tuned)."""
+    count = lib().gee_tune_get(None, 0)
+    buf = (_lib_mod.TuneCell * max(count, 1))()
+    got = lib().gee_tune_get(buf, count)
+    out = []
+    for i in range(min(got, count)):
+        c = buf[i]
+        out.append({"log2_cells": c.log2_cells, "log2_density": c.log2_density,
+                    "strategy": STRATEGY_NAMES[c.strategy], "block": c.block,
+                    "ms_atomic": c.ms_atomic, "ms_private": c.ms_private,
+                    "ms_segmented": c.ms_segmented})
+    return out
+
+
+def tune_set(table) -> None:
+    """Install a tuning table (as returned by tune_table); [] resets."""
+    buf = (_lib_mod.TuneCell * max(len(table), 1))()
+    for i, c in enumerate(table):
+        buf[i].log2_cells = int(c["log2_cells"])
+        buf[i].log2_density = int(c["log2_density"])
+        st = c["strategy"]
+        buf[i].strategy = STRATEGIES[st] if isinstance(st, str) else int(st)
+        buf[i].block = int(c.get("block", 0))
+        buf[i].ms_atomic = float(c.get("ms_atomic", -1))
+        buf[i].ms_private = float(c.get("ms_private", -1))
+        buf[i].ms_segmented = float(c.get("ms_segmented", -1))
+    check(lib().gee_tune_set(buf, len(table)), "gee_tune_set")
+
+
+def autotune(effort: int = 0, stream=None) -> list:
+    """gee_autotune: time the edge-list strategies on this device and
+    install the fastest per problem shape for GEE_AUTO; returns the table."""
+    check(lib().gee_autotune(int(effort), _stream_handle(stream)), "gee_autotune")
+    return tune_table()
 
 
 def embed_noalloc(edges, Y, K: int, weights=None, *, out=None, stream=None):

@@ -73,6 +73,20 @@ class Problem(ctypes.Structure):
     ]
 
 
+class TuneCell(ctypes.Structure):
+    """gee_tune_cell: one grid point of the GEE_AUTO tuning table."""
+    _fields_ = [
+        ("log2_cells", ctypes.c_int32),
+        ("log2_density", ctypes.c_int32),
+        ("strategy", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("ms_atomic", ctypes.c_float),
+        ("ms_private", ctypes.c_float),
+        ("ms_segmented", ctypes.c_float),
+        ("reserved", ctypes.c_float),
+    ]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_bytes", ctypes.c_int64),
@@ -129,6 +143,9 @@ SIGNATURES = {
     "gee_embed_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
     "gee_embed_batch": (ctypes.c_int, [ctypes.POINTER(Problem), _I32,
                                        ctypes.POINTER(ctypes.c_int), _OPT, _P]),
+    "gee_autotune": (ctypes.c_int, [_I32, _P]),
+    "gee_tune_get": (_I32, [ctypes.POINTER(TuneCell), _I32]),
+    "gee_tune_set": (ctypes.c_int, [ctypes.POINTER(TuneCell), _I32]),
     "gee_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
     "gee_server_add_graph": (ctypes.c_int, [_P, _P, _P, _I64, _I64, ctypes.POINTER(_I64)]),
     "gee_server_drop_graph": (ctypes.c_int, [_P, _I64]),

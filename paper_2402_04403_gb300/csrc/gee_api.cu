@@ -276,7 +276,13 @@ gee_status embed_coo(Workspace &ws, const int32_t *E, const float *w,
     if (rc != GEE_OK)
         return rc;
     const gee_strategy strat = gee_pick_strategy(s, n, K, &o);
-    const int threads = o.block != 0 ? o.block : 256;
+    int threads = o.block != 0 ? o.block : 256;
+    if (o.strategy == GEE_AUTO && o.block == 0) {
+        gee_strategy tuned;
+        int32_t block = 0;
+        if (tuned_choice(s, n, K, &tuned, &block) && tuned == strat && block != 0)
+            threads = block;
+    }
     if (strat == GEE_SEGMENTED) {
         Csr g;
         GEE_CHECK_CUDA(build_csr(E, w, s, n, ws, ws, g, st, stream));
@@ -485,6 +491,10 @@ gee_strategy gee_pick_strategy(int64_t s, int64_t n, int32_t K,
         return GEE_ATOMIC;  // the copy would not fit in shared memory
     if (o.strategy != GEE_AUTO)
         return static_cast<gee_strategy>(o.strategy);
+    gee_strategy tuned;
+    int32_t tuned_block = 0;
+    if (tuned_choice(s, n, K, &tuned, &tuned_block))
+        return tuned == GEE_PRIVATE && cells > limit ? GEE_ATOMIC : tuned;
     const int64_t cap =
         o.private_max_cells > 0 && o.private_max_cells < limit
             ? o.private_max_cells

@@ -641,8 +641,9 @@ struct TileCells {
 
 // Adds the arcs [0, NA) that start at colp[0] (any alignment) with NT
 // threads, t = this thread: 16-byte loads of four arcs for the aligned body
-// (full rounds of kUnroll arcs per thread unguarded, then a guarded rest),
-// single arcs for the head and tail.  cells maps (arc, label) to an
+// in rounds of kUnroll arcs per thread -- the next round's arcs are loaded
+// before this round's labels are gathered, so the two latencies overlap --
+// and single arcs for the head and tail.  cells maps (arc, label) to an
 // accumulator index; arcs whose label is unknown go to this thread's own
 // sink cell (no branch, no shared-address contention).
 template <bool WEIGHTED, bool MULTI, int NT, class Cells>
@@ -705,17 +706,24 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
     const int4 *col4 = reinterpret_cast<const int4 *>(colp + head);
     const float4 *val4 = reinterpret_cast<const float4 *>(valp + head);
     constexpr int kQ = kUnroll / 4;  // quads per thread per round
-    auto round = [&](int q0, bool guard) {
-        int4 c[kQ];
-        float4 w[kQ];
+    auto quads = [&](int q0, int4 (&c)[kQ], float4 (&w)[kQ]) {
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
             const int q = q0 + u * NT;
-            const bool ok = !guard || q < nq;
+            const bool ok = q < nq;
             c[u] = ok ? __ldcs(col4 + q) : make_int4(0, 0, 0, 0);
             if (WEIGHTED)
                 w[u] = ok ? __ldcs(val4 + q) : make_float4(0, 0, 0, 0);
         }
+    };
+    int4 c[kQ];
+    float4 w[kQ];
+    if (t < nq)
+        quads(t, c, w);
+    for (int q0 = t; q0 < nq; q0 += kQ * NT) {
+        int4 cn[kQ];
+        float4 wn[kQ];
+        quads(q0 + kQ * NT, cn, wn);  // next round's arcs, in flight now
         uint32_t y[kUnroll];
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
@@ -727,7 +735,7 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
 #pragma unroll
         for (int u = 0; u < kQ; ++u) {
             const int q = q0 + u * NT;
-            if (!guard || q < nq) {
+            if (q < nq) {
                 const int i0 = head + 4 * q;
                 cells.at(i0);
                 add(i0 + 0, y[4 * u + 0], WEIGHTED ? w[u].x : 0.0f);
@@ -736,12 +744,12 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                 add(i0 + 3, y[4 * u + 3], WEIGHTED ? w[u].w : 0.0f);
             }
         }
-    };
-    const int full = nq / (kQ * NT) * (kQ * NT);
-    for (int q0 = t; q0 < full; q0 += kQ * NT)
-        round(q0, false);
-    if (full + t < nq)
-        round(full + t, true);
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            c[u] = cn[u];
+            w[u] = wn[u];
+        }
+    }
     const int tail0 = head + 4 * nq;
     if (t < NA - tail0) {
         cells.at(tail0 + t);

@@ -335,6 +335,12 @@ cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
                           const BatchHeader &hh, bool validate,
                           cudaStream_t stream);
 
+// ------------------------------------------------------------ autotuner
+// The tuned GEE_AUTO choice for an edge-list problem (gee_tune.cu); false
+// when the current device has no table.
+bool tuned_choice(int64_t s, int64_t n, int32_t K, gee_strategy *strategy,
+                  int32_t *block);
+
 // ------------------------------------------------------------ runtime
 // S1-S5 of L label vectors (Y[l*n + i], L >= 1) on a resident graph,
 // enqueued on `stream` without waiting: *st receives the call's device

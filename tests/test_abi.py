@@ -146,3 +146,29 @@ def test_server_argument_checks_need_no_gpu(gee):
     if not torch.cuda.is_available():
         rc = lib.gee_server_create(None, ctypes.byref(h))
         assert rc != 0 and not h.value
+
+
+def test_tuning_table_drives_auto_without_a_gpu(gee):
+    """An installed tuning table decides GEE_AUTO by the nearest grid point
+    in (log2 n*K, log2 density); an empty table restores the built-in rule."""
+    try:
+        gee.tune_set([
+            {"log2_cells": 12, "log2_density": 0, "strategy": "segmented", "block": 0},
+            {"log2_cells": 20, "log2_density": 0, "strategy": "atomic", "block": 512},
+            {"log2_cells": 12, "log2_density": 4, "strategy": "private", "block": 0},
+        ])
+        assert [c["strategy"] for c in gee.tune_table()] == ["segmented", "atomic", "private"]
+        # n*K = 4096 cells, density 1 -> segmented
+        assert gee.pick_strategy(2048, 256, 16) == "segmented"
+        # n*K = 2^21, density 1 -> nearest is the 2^20 point
+        assert gee.pick_strategy(1 << 20, 1 << 17, 16) == "atomic"
+        # dense small problem -> private
+        assert gee.pick_strategy(32768, 256, 16) == "private"
+        # an explicit strategy is not overridden
+        assert gee.pick_strategy(2048, 256, 16, strategy="atomic") == "atomic"
+        with pytest.raises(gee.GeeError):
+            gee.tune_set([{"log2_cells": 1, "log2_density": 0, "strategy": 0}])
+    finally:
+        gee.tune_set([])
+    assert gee.tune_table() == []
+    assert gee.pick_strategy(2048, 256, 16) in ("atomic", "private")
