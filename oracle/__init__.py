@@ -74,9 +74,11 @@ def _lib():
             lib.gee_oracle_embed_rows.argtypes = [p, p, i64, p, i64, i32, ci,
                                                   p, i64, p, p]
             lib.gee_oracle_set_mutation.argtypes = [ci]
+            lib.gee_oracle_unsupervised.argtypes = [p, i64, i64, i32, i32, p, p, p]
             for f in (lib.gee_oracle_class_counts, lib.gee_oracle_degrees,
                       lib.gee_oracle_embed, lib.gee_oracle_counts,
-                      lib.gee_oracle_round_counts, lib.gee_oracle_embed_rows):
+                      lib.gee_oracle_round_counts, lib.gee_oracle_embed_rows,
+                      lib.gee_oracle_unsupervised):
                 f.restype = ci
             lib.gee_oracle_set_mutation.restype = None
             _LIB = lib
@@ -185,3 +187,16 @@ def embed_rows(edges, Y, K: int, rows, weights=None, laplacian: bool = False,
                                         y.size, K, int(bool(laplacian)),
                                         _ptr(r), r.size, _ptr(Z), _ptr(C)))
     return (r, Z, C) if with_counts else (r, Z)
+
+
+def unsupervised(edges, Y0, K: int, max_iter: int = 50):
+    """Unsupervised GEE (gee_oracle_unsupervised): alternate the unit-weight
+    embedding with one k-means assignment step from labels Y0 (all known).
+    Returns (labels, rounds, moved per round)."""
+    e = _edges(edges)
+    y = np.array(Y0, dtype=np.int32, copy=True)
+    rounds = ctypes.c_int32()
+    changes = np.zeros(max(max_iter, 1), dtype=np.int64)
+    _check(_lib().gee_oracle_unsupervised(_ptr(e), e.shape[0], y.size, int(K), int(max_iter),
+                                          _ptr(y), ctypes.byref(rounds), _ptr(changes)))
+    return y, rounds.value, changes[:rounds.value].tolist()

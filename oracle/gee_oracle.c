@@ -63,6 +63,7 @@
  *   6  Laplacian: scale by 1/d_u instead of 1/sqrt(d_u d_v)
  *   7  self-loop applied once
  *   8  class sizes count unknown labels as class K-1
+ *   9  unsupervised loop: centroids divided by m_k only (not m_k * m_j)
  */
 int gee_oracle_mutation = 0;
 
@@ -372,5 +373,95 @@ int gee_oracle_embed_rows(const int32_t *E, const float *w, int64_t s,
     free(d);
     free(bitmap);
     free(nk);
+    return ORC_OK;
+}
+
+/*
+ * Unsupervised GEE.  Section II notes that Y may come from unsupervised
+ * clustering instead of known labels; here the clustering is k-means on the
+ * embedding itself (Lloyd, "Least squares quantization in PCM", IEEE Trans.
+ * Inf. Theory 1982), alternated with Alg. 1 from the given starting labels:
+ * each round embeds the current labels and moves every node to the nearest
+ * class mean of that embedding, until a round changes no label or max_iter
+ * rounds ran.  Unit weights, every label known (0..K-1).  With
+ *   C       integer counts of the current labels (Alg. 1, unit weights)
+ *   m_k     class sizes
+ *   Z[i,j]  = C[i,j] / m_j                         (FP64, one division)
+ *   S[k,j]  = sum of C[i,j] over i of class k      (exact integers)
+ *   c[k,j]  = S[k,j] / (m_k * m_j)                 (FP64 product, then one division)
+ *   d(i,k)  = sum over j = 0..K-1, in that order, of (Z[i,j] - c[k,j])^2
+ *             (each difference, square and sum rounded separately)
+ * node i moves to the k with the smallest d(i,k) among classes with
+ * m_k > 0, the lowest k on ties.  The labels are updated in place in Y;
+ * *rounds receives the number of rounds run (the last one changed nothing
+ * unless max_iter ended the loop) and changes[r] (if not NULL, length
+ * max_iter) the number of nodes round r moved.
+ */
+int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
+                            int32_t max_iter, int32_t *Y, int32_t *rounds,
+                            int64_t *changes)
+{
+    if (rounds == NULL || max_iter < 0)
+        return ORC_BAD_ARG;
+    *rounds = 0;
+    int st = check_inputs(E, NULL, s, Y, n, K, 0);
+    if (st != ORC_OK)
+        return st;
+    for (int64_t i = 0; i < n; ++i)
+        if (Y[i] < 0)
+            return ORC_BAD_LABEL;
+    uint64_t *C = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1) * (size_t)K);
+    uint64_t *S = malloc(sizeof(uint64_t) * (size_t)K * (size_t)K);
+    double *cen = malloc(sizeof(double) * (size_t)K * (size_t)K);
+    int64_t *m = malloc(sizeof(int64_t) * (size_t)K);
+    int32_t *next = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!C || !S || !cen || !m || !next) {
+        free(C); free(S); free(cen); free(m); free(next);
+        return ORC_NO_MEMORY;
+    }
+    for (int32_t r = 0; r < max_iter; ++r) {
+        gee_oracle_counts(E, s, Y, n, K, C);
+        gee_oracle_class_counts(Y, n, K, m);
+        memset(S, 0, sizeof(uint64_t) * (size_t)K * (size_t)K);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t j = 0; j < K; ++j)
+                S[(int64_t)Y[i] * K + j] += C[i * K + j];
+        for (int32_t k = 0; k < K; ++k)
+            for (int32_t j = 0; j < K; ++j) {
+                double den = (gee_oracle_mutation == 9)
+                                 ? (double)m[k]
+                                 : (double)m[k] * (double)m[j];
+                cen[k * K + j] = den > 0.0 ? (double)S[k * K + j] / den : 0.0;
+            }
+        int64_t moved = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t best = -1;
+            double bd = 0.0;
+            for (int32_t k = 0; k < K; ++k) {
+                if (m[k] == 0)
+                    continue;
+                double d = 0.0;
+                for (int32_t j = 0; j < K; ++j) {
+                    double z = m[j] > 0 ? (double)C[i * K + j] / (double)m[j] : 0.0;
+                    double diff = z - cen[k * K + j];
+                    double sq = diff * diff;
+                    d = d + sq;
+                }
+                if (best < 0 || d < bd) {
+                    best = k;
+                    bd = d;
+                }
+            }
+            next[i] = best;
+            moved += (best != Y[i]);
+        }
+        memcpy(Y, next, sizeof(int32_t) * (size_t)n);
+        if (changes != NULL)
+            changes[r] = moved;
+        *rounds = r + 1;
+        if (moved == 0)
+            break;
+    }
+    free(C); free(S); free(cen); free(m); free(next);
     return ORC_OK;
 }

@@ -249,6 +249,77 @@ def test_error_codes():
     assert ei.value.code == oracle.BAD_WEIGHT
 
 
+# ---------------------------------------------------------------------------
+# Unsupervised GEE: embedding alternated with k-means assignment steps
+# ---------------------------------------------------------------------------
+def _exact_round(edges, Y, K):
+    """One round written out with exact rationals, independently of the
+    oracle: integer counts by a loop over the edges, class means, squared
+    distances; returns the new labels and, per node, the gap between the
+    best and the second-best distance (0 for ties)."""
+    n = len(Y)
+    C = [[0] * K for _ in range(n)]
+    for u, v in edges:
+        C[u][Y[v]] += 1
+        C[v][Y[u]] += 1
+    m = [sum(1 for y in Y if y == k) for k in range(K)]
+    Z = [[Fraction(C[i][j], m[j]) if m[j] else Fraction(0) for j in range(K)]
+         for i in range(n)]
+    cen = [[Fraction(sum(C[i][j] for i in range(n) if Y[i] == k), m[k] * m[j])
+            if m[k] and m[j] else Fraction(0) for j in range(K)] for k in range(K)]
+    new, gaps = [], []
+    for i in range(n):
+        d = sorted((sum((Z[i][j] - cen[k][j]) ** 2 for j in range(K)), k)
+                   for k in range(K) if m[k])
+        new.append(d[0][1])
+        gaps.append(d[1][0] - d[0][0] if len(d) > 1 else Fraction(1))
+    return new, gaps
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_unsupervised_round_matches_exact_rationals(seed):
+    """One round (embed, then move every node to the nearest class mean)
+    equals the exact-rational computation wherever the nearest mean is not
+    within 1e-9 of the next one (FP64 decides only near-ties)."""
+    rng = np.random.default_rng(seed)
+    n, K = 14, 3
+    edges = graphgen.random_graph(n, 30, seed=100 + seed)
+    Y0 = rng.integers(0, K, n).astype(np.int32)
+    Y0[:K] = np.arange(K)  # every class present
+    want, gaps = _exact_round([tuple(e) for e in edges.tolist()], Y0.tolist(), K)
+    got, rounds, moved = oracle.unsupervised(edges, Y0, K, max_iter=1)
+    assert rounds == 1 and moved[0] == int(np.sum(got != Y0))
+    clear = [i for i in range(n) if gaps[i] > Fraction(1, 10**9)]
+    assert len(clear) >= n // 2
+    assert [int(got[i]) for i in clear] == [want[i] for i in clear]
+
+
+def test_unsupervised_recovers_planted_blocks():
+    """A planted partition with p_in/p_out = 50: the true blocks are a fixed
+    point (one round, nothing moves); from 20% corrupted labels the loop
+    returns to them; from random labels it finds them up to a relabelling;
+    a class left empty by the start labels is never chosen."""
+    import itertools
+    n, K = 600, 3
+    edges = graphgen.planted_edges(n, K, 6000, 50.0, seed=1)
+    truth = graphgen.planted_labels(n, K)
+    y, rounds, moved = oracle.unsupervised(edges, truth, K)
+    assert rounds == 1 and moved == [0] and np.array_equal(y, truth)
+    rng = np.random.default_rng(0)
+    y0 = truth.copy()
+    flip = rng.random(n) < 0.2
+    y0[flip] = rng.integers(0, K, int(flip.sum()))
+    y, rounds, moved = oracle.unsupervised(edges, y0, K)
+    assert np.array_equal(y, truth) and moved[-1] == 0
+    y, rounds, moved = oracle.unsupervised(edges, rng.integers(0, K, n).astype(np.int32), K)
+    best = max(np.mean(np.array(p)[y] == truth) for p in itertools.permutations(range(K)))
+    assert best == 1.0 and moved[-1] == 0
+    y4, _, _ = oracle.unsupervised(edges, truth, K + 1)
+    assert np.all(y4 < K)
+    with pytest.raises(oracle.OracleError):
+        oracle.unsupervised(edges, np.where(truth == 0, -1, truth).astype(np.int32), K)
+
+
 def _pins_all_hold() -> bool:
     """Run a compact subset of the pins above; False if any fails."""
     try:
@@ -260,12 +331,14 @@ def _pins_all_hold() -> bool:
         test_single_class_is_degree_over_n()
         for seed in range(2):
             test_laplacian_matches_scipy_normalised_laplacian(seed, True)
+        for seed in range(3):
+            test_unsupervised_round_matches_exact_rationals(seed)
     except AssertionError:
         return False
     return True
 
 
-@pytest.mark.parametrize("mutation", range(1, 9))
+@pytest.mark.parametrize("mutation", range(1, 10))
 def test_pins_catch_planted_mistakes(mutation):
     """Each planted oracle mistake (dropped update, wrong index, transposed
     row, wrong class size, ...) must make at least one pin fail."""
