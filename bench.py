@@ -75,6 +75,12 @@ WORKLOADS = {
                             "paper-scale graph (sampled rows)",
                       rows=4096, seed=6, weighted=False, laplacian=False,
                       scale=0, n=0, s=0, K=0),
+    "unsup": dict(desc="unsupervised GEE: planted partition (edge-sampling SBM, p_in/p_out = "
+                        "10), n = 2^24, s = 2^28 unit-weight edges, K = 16 blocks; starting "
+                        "labels: the planted block for 10% of nodes, uniform random for the "
+                        "rest; rounds of embedding + k-means assignment until nothing moves",
+                  n=1 << 24, s=1 << 28, K=16, ratio=10.0, max_iter=40, known=0.1, seed=7,
+                  weighted=False, laplacian=False, scale=0),
     "rmat24lap": dict(desc="R-MAT scale 24 weighted, Laplacian variant",
                       scale=24, n=1 << 24, s=268_435_456, K=20, frac_unlabeled=0.1,
                       weighted=True, laplacian=True, seed=2),
@@ -801,6 +807,67 @@ def run_precision(args, w, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_unsup(args, w, world, rank, local):
+    """Unsupervised GEE (gee_unsupervised) on a planted partition: rounds,
+    nodes moved per round, time per round and agreement with the planted
+    blocks."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2402_04403_gb300 as gee
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, s, K = w["n"], w["s"], w["K"]
+    edges = graphgen.planted_edges_device(n, K, s, w["ratio"], w["seed"], device=dev)
+    truth = graphgen.planted_labels_device(n, K, device=dev)
+    noise = graphgen.labels_device(n, K, w["seed"] + 1, 0.0, device=dev)
+    keep = graphgen.labels_device(n, 1 << 20, w["seed"] + 2, 0.0, device=dev) < int(
+        w["known"] * (1 << 20))
+    Y0 = torch.where(keep, truth, noise)
+    g = gee.Graph(edges, n)
+    del edges
+    g.unsupervised(Y0, K, max_iter=1)  # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    y, Z, rounds, moved = g.unsupervised(Y0, K, max_iter=w["max_iter"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    gee.profile_read()
+    gee.profile_enable(True)
+    g.unsupervised(Y0, K, max_iter=2)
+    torch.cuda.synchronize()
+    gee.profile_enable(False)
+    kernels = {k: {"launches": v["launches"], "ms": v["total_ms"] / max(v["launches"], 1)}
+               for k, v in gee.profile_read().items()}
+    # agreement: each found class counted by its most frequent planted block
+    conf = torch.zeros(K * K, dtype=torch.int64, device=dev)
+    conf.index_add_(0, (y.long() * K + truth.long()),
+                    torch.ones(n, dtype=torch.int64, device=dev))
+    conf = conf.view(K, K).cpu().numpy()
+    purity = float(conf.max(axis=1).sum() / n)
+    g.close()
+    line = {
+        "metric": "unsupervised GEE: time per round (embedding + k-means assignment)",
+        "value": ms / max(rounds, 1), "unit": "ms/round", "higher_is_better": False,
+        "n_gpus": world, "steps": rounds, "warmup": 1, "ms_per_step": ms / max(rounds, 1),
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "name": args.workload, "n": n, "s": s, "K": K,
+                   "max_iter": w["max_iter"], "parallelism": "replicas"},
+        "rounds": rounds, "moved_per_round": moved, "total_ms": ms,
+        "edges_per_s_per_round": s / (ms / max(rounds, 1) / 1e3),
+        "purity_vs_planted_blocks": purity, "kernels_per_launch": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w, world, rank, local):
     import torch
 
@@ -961,7 +1028,7 @@ def main():
         ap.error("need --steps >= 1 and --warmup >= 0")
     w = dict(WORKLOADS[args.workload])
     if args.scale_shift and "graphs" not in w and "pool" not in w and \
-            args.workload != "precision":
+            args.workload not in ("precision", "unsup"):
         sh = args.scale_shift
         w.update(scale=w["scale"] - sh, n=w["n"] >> sh, s=w["s"] >> sh,
                  desc=w["desc"] + f" (shrunk by 2^{sh}: n={w['n'] >> sh}, s={w['s'] >> sh})")
@@ -976,6 +1043,8 @@ def main():
         run_serve(args, w, world, rank, local)
     elif args.workload == "precision":
         run_precision(args, w, world, rank, local)
+    elif args.workload == "unsup":
+        run_unsup(args, w, world, rank, local)
     else:
         run_ours(args, w, world, rank, local)
     if world > 1:

@@ -200,6 +200,32 @@ GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
                            const gee_options *opts);
 
 /*
+ * Unsupervised GEE on a resident unweighted graph.  Section II allows Y to
+ * come from unsupervised clustering; the clustering here is k-means on the
+ * embedding (Lloyd's assignment step), alternated with the pass: each round
+ * embeds the current labels and moves every node to the nearest class mean
+ * of that embedding, until a round moves no node or max_iter rounds ran.
+ *   Y      device int32 [n], the starting labels, every one in 0..K-1;
+ *          updated in place to the final labels
+ *   K      1..64
+ *   Z      device float [n][K]: the embedding of the final labels
+ *   rounds host: rounds run (the last moved nothing unless max_iter ended
+ *          the loop); moved: host int64 [max_iter] nodes moved per round,
+ *          or NULL
+ * With C the exact neighbour counts, m_k the class sizes, Z = RN32(C/m_j)
+ * and S[k][j] the exact class sums of C, node i moves to the non-empty class
+ * k with the smallest sum over j = 0..K-1 (in order, FP32, each operation
+ * rounded on its own) of (Z[i][j] - RN32(S[k][j]/(m_k m_j)))^2, the lowest k
+ * on ties, so every run takes the same decisions.  Counts must stay below
+ * 2^23.
+ * GEE_ERR_UNSUPPORTED for weighted graphs or K > 64.
+ */
+GEE_API gee_status gee_unsupervised(gee_graph *graph, int32_t *Y, int32_t K,
+                                    int32_t max_iter, float *Z,
+                                    int32_t *rounds, int64_t *moved,
+                                    gee_stream_t stream);
+
+/*
  * Autotuning of GEE_AUTO for edge-list calls (no counterpart in the paper).
  * gee_autotune times ATOMIC (block sizes 128, 256, 512), PRIVATE (where Z
  * fits in shared memory) and SEGMENTED on seeded synthetic problems (K = 16,

@@ -386,13 +386,14 @@ int gee_oracle_embed_rows(const int32_t *E, const float *w, int64_t s,
  * rounds ran.  Unit weights, every label known (0..K-1).  With
  *   C       integer counts of the current labels (Alg. 1, unit weights)
  *   m_k     class sizes
- *   Z[i,j]  = C[i,j] / m_j                         (FP64, one division)
+ *   Z[i,j]  = RN32(C[i,j] / m_j), the float embedding of the count path
  *   S[k,j]  = sum of C[i,j] over i of class k      (exact integers)
- *   c[k,j]  = S[k,j] / (m_k * m_j)                 (FP64 product, then one division)
+ *   c[k,j]  = RN32(S[k,j] / (m_k * m_j))           (quotient formed in FP64)
  *   d(i,k)  = sum over j = 0..K-1, in that order, of (Z[i,j] - c[k,j])^2
- *             (each difference, square and sum rounded separately)
+ *             in FP32, each difference, square and sum rounded separately
  * node i moves to the k with the smallest d(i,k) among classes with
- * m_k > 0, the lowest k on ties.  The labels are updated in place in Y;
+ * m_k > 0, the lowest k on ties.  (The paper fixes no precision for the
+ * clustering step; distances are taken in the precision of the embedding.)  The labels are updated in place in Y;
  * *rounds receives the number of rounds run (the last one changed nothing
  * unless max_iter ended the loop) and changes[r] (if not NULL, length
  * max_iter) the number of nodes round r moved.
@@ -412,7 +413,7 @@ int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
             return ORC_BAD_LABEL;
     uint64_t *C = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1) * (size_t)K);
     uint64_t *S = malloc(sizeof(uint64_t) * (size_t)K * (size_t)K);
-    double *cen = malloc(sizeof(double) * (size_t)K * (size_t)K);
+    float *cen = malloc(sizeof(float) * (size_t)K * (size_t)K);
     int64_t *m = malloc(sizeof(int64_t) * (size_t)K);
     int32_t *next = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     if (!C || !S || !cen || !m || !next) {
@@ -431,20 +432,23 @@ int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
                 double den = (gee_oracle_mutation == 9)
                                  ? (double)m[k]
                                  : (double)m[k] * (double)m[j];
-                cen[k * K + j] = den > 0.0 ? (double)S[k * K + j] / den : 0.0;
+                cen[k * K + j] =
+                    den > 0.0 ? (float)((double)S[k * K + j] / den) : 0.0f;
             }
         int64_t moved = 0;
         for (int64_t i = 0; i < n; ++i) {
             int32_t best = -1;
-            double bd = 0.0;
+            float bd = 0.0f;
             for (int32_t k = 0; k < K; ++k) {
                 if (m[k] == 0)
                     continue;
-                double d = 0.0;
+                float d = 0.0f;
                 for (int32_t j = 0; j < K; ++j) {
-                    double z = m[j] > 0 ? (double)C[i * K + j] / (double)m[j] : 0.0;
-                    double diff = z - cen[k * K + j];
-                    double sq = diff * diff;
+                    float z = m[j] > 0
+                                  ? (float)((double)C[i * K + j] / (double)m[j])
+                                  : 0.0f;
+                    float diff = z - cen[k * K + j];
+                    float sq = diff * diff;
                     d = d + sq;
                 }
                 if (best < 0 || d < bd) {

@@ -328,6 +328,23 @@ class Graph:
         check(rc, "gee_embed_graph_multi")
         return out
 
+    def unsupervised(self, Y0, K: int, max_iter: int = 50, *, out=None, stream=None):
+        """Unsupervised GEE (gee_unsupervised) from device labels Y0 (every
+        label in 0..K-1): returns (labels, Z, rounds, moved per round)."""
+        import numpy as np
+        torch = _torch()
+        Y = Y0.clone()
+        if out is None:
+            out = torch.empty((self.n, K), dtype=torch.float32, device=Y.device)
+        rounds = ctypes.c_int32()
+        moved = np.zeros(max(int(max_iter), 1), dtype=np.int64)
+        rc = lib().gee_unsupervised(
+            self.handle, _dev_ptr(Y, torch.int32, "Y", (self.n,)), int(K), int(max_iter),
+            _dev_ptr(out, torch.float32, "out", (self.n, K)), ctypes.byref(rounds),
+            ctypes.c_void_p(moved.ctypes.data), _stream_handle(stream))
+        check(rc, "gee_unsupervised")
+        return Y, out, rounds.value, moved[:rounds.value].tolist()
+
     def embed_host(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
         import numpy as np
         Yv = _host_buf(Y)

@@ -143,6 +143,8 @@ SIGNATURES = {
     "gee_embed_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
     "gee_embed_batch": (ctypes.c_int, [ctypes.POINTER(Problem), _I32,
                                        ctypes.POINTER(ctypes.c_int), _OPT, _P]),
+    "gee_unsupervised": (ctypes.c_int, [_P, _P, _I32, _I32, _P, ctypes.POINTER(_I32),
+                                        _P, _P]),
     "gee_autotune": (ctypes.c_int, [_I32, _P]),
     "gee_tune_get": (_I32, [ctypes.POINTER(TuneCell), _I32]),
     "gee_tune_set": (ctypes.c_int, [ctypes.POINTER(TuneCell), _I32]),

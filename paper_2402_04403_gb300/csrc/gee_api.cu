@@ -403,6 +403,8 @@ gee_status ensure_laplacian(gee_graph *g, cudaStream_t stream)
 
 }  // namespace
 
+bool gee::graph_weighted(const gee_graph *graph) { return graph->csr.weighted; }
+
 gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                                    const int32_t *Y, int32_t L, int32_t K,
                                    int32_t laplacian, float *Z,

@@ -345,6 +345,7 @@ bool tuned_choice(int64_t s, int64_t n, int32_t K, gee_strategy *strategy,
 // S1-S5 of L label vectors (Y[l*n + i], L >= 1) on a resident graph,
 // enqueued on `stream` without waiting: *st receives the call's device
 // status word (in ws).  Z is [n][L*K].  Argument checks are the caller's.
+bool graph_weighted(const gee_graph *graph);
 gee_status graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                               const int32_t *Y, int32_t L, int32_t K,
                               int32_t laplacian, float *Z, DevStatus **st,

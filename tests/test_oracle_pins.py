@@ -272,15 +272,17 @@ def _exact_round(edges, Y, K):
         d = sorted((sum((Z[i][j] - cen[k][j]) ** 2 for j in range(K)), k)
                    for k in range(K) if m[k])
         new.append(d[0][1])
-        gaps.append(d[1][0] - d[0][0] if len(d) > 1 else Fraction(1))
+        gaps.append((d[1][0] - d[0][0]) / (d[0][0] + Fraction(1, 10**6))
+                    if len(d) > 1 else Fraction(1))
     return new, gaps
 
 
 @pytest.mark.parametrize("seed", range(6))
 def test_unsupervised_round_matches_exact_rationals(seed):
     """One round (embed, then move every node to the nearest class mean)
-    equals the exact-rational computation wherever the nearest mean is not
-    within 1e-9 of the next one (FP64 decides only near-ties)."""
+    equals the exact-rational computation wherever the nearest mean is
+    clearly nearer than the next one (gap above 1e-4 of the distance; the
+    FP32 distances decide only near-ties)."""
     rng = np.random.default_rng(seed)
     n, K = 14, 3
     edges = graphgen.random_graph(n, 30, seed=100 + seed)
@@ -289,7 +291,7 @@ def test_unsupervised_round_matches_exact_rationals(seed):
     want, gaps = _exact_round([tuple(e) for e in edges.tolist()], Y0.tolist(), K)
     got, rounds, moved = oracle.unsupervised(edges, Y0, K, max_iter=1)
     assert rounds == 1 and moved[0] == int(np.sum(got != Y0))
-    clear = [i for i in range(n) if gaps[i] > Fraction(1, 10**9)]
+    clear = [i for i in range(n) if gaps[i] > Fraction(1, 10**4)]
     assert len(clear) >= n // 2
     assert [int(got[i]) for i in clear] == [want[i] for i in clear]
 
