@@ -199,11 +199,58 @@ gee_status labels_step(Workspace &ws, const int32_t *Y, int64_t n, int32_t K,
     return labels_launch(Y, n, K, rank, *Yc, *counts, *st, stream);
 }
 
+// Fork/join of a side stream for work that overlaps the call's stream.
+class SideStream {
+  public:
+    explicit SideStream(cudaStream_t main) : main_(main) {}
+    ~SideStream()
+    {
+        if (fork_)
+            cudaEventDestroy(fork_);
+        if (join_)
+            cudaEventDestroy(join_);
+        if (side_)
+            cudaStreamDestroy(side_);  // released once its work is done
+    }
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    cudaError_t fork()
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&join_, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(fork_, main_);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(side_, fork_, 0);
+        return e;
+    }
+    cudaError_t join()
+    {
+        cudaError_t e = cudaEventRecord(join_, side_);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(main_, join_, 0);
+        return e;
+    }
+    cudaStream_t stream() const { return side_; }
+
+  private:
+    cudaStream_t main_;
+    cudaStream_t side_ = nullptr;
+    cudaEvent_t fork_ = nullptr, join_ = nullptr;
+};
+
 // S4 + S5 over a CSR (resident or built for this call), for L label
-// vectors of K classes (Z rows of L*K columns).
+// vectors of K classes (Z rows of L*K columns).  host_z: Z is page-locked
+// host memory, so the row tiles are bound by the host link; they then run
+// on a quarter of the SMs while the hub chunks run on the rest at the same
+// time (partial sums only), and the fixup writes every hub row after both.
 gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                      const uint8_t *Yc, const uint32_t *counts, float *Z,
-                     const DevStatus *st, cudaStream_t stream, int32_t L = 1)
+                     const DevStatus *st, cudaStream_t stream, int32_t L = 1,
+                     bool host_z = false)
 {
     const int32_t cols = L * K;
     if (L >= kWideMinLabels) {
@@ -226,7 +273,8 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         if (g.hubs > 0) {
             ProfScope p("k_hub_fixup", stream);
             GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
-                                            counts, Z, hub_part, st, stream));
+                                            counts, Z, hub_part, false, st,
+                                            stream));
         }
         return GEE_OK;
     }
@@ -243,6 +291,32 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         ProfScope p("k_partition", stream);
         GEE_CHECK_CUDA(launch_partition(g, cols, tile_row, ntiles, stream));
     }
+    if (host_z && g.chunks > 0) {
+        const int sms = sm_count();
+        const int light_ctas = sms / 4 > 0 ? sms / 4 : 1;
+        SideStream side(stream);
+        GEE_CHECK_CUDA(side.fork());
+        {
+            ProfScope p("k_pull_heavy", side.stream());
+            GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
+                                             counts, Z, hub_part, true, st,
+                                             side.stream(), sms - light_ctas));
+        }
+        {
+            ProfScope p("k_pull_light", stream);
+            GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
+                                             tile_row, ntiles, Yc, counts, Z,
+                                             work, st, stream, light_ctas));
+        }
+        GEE_CHECK_CUDA(side.join());
+        if (g.hubs > 0) {
+            ProfScope p("k_hub_fixup", stream);
+            GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
+                                            counts, Z, hub_part, true, st,
+                                            stream));
+        }
+        return GEE_OK;
+    }
     {
         ProfScope p("k_pull_light", stream);
         GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
@@ -252,12 +326,13 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
     if (g.chunks > 0) {
         ProfScope p("k_pull_heavy", stream);
         GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
-                                         counts, Z, hub_part, st, stream));
+                                         counts, Z, hub_part, false, st,
+                                         stream));
     }
     if (g.hubs > 0) {
         ProfScope p("k_hub_fixup", stream);
         GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian, counts,
-                                        Z, hub_part, st, stream));
+                                        Z, hub_part, false, st, stream));
     }
     return GEE_OK;
 }
@@ -408,7 +483,8 @@ bool gee::graph_weighted(const gee_graph *graph) { return graph->csr.weighted; }
 gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                                    const int32_t *Y, int32_t L, int32_t K,
                                    int32_t laplacian, float *Z,
-                                   DevStatus **st_out, cudaStream_t stream)
+                                   DevStatus **st_out, cudaStream_t stream,
+                                   bool host_z)
 {
     if (laplacian) {
         gee_status rc = ensure_laplacian(graph, stream);
@@ -435,18 +511,19 @@ gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
         return rc;
     *st_out = st;
     return pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
-                     stream, L);
+                     stream, L, host_z);
 }
 
 namespace {
 
 gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
                            int32_t K, int32_t laplacian, float *Z,
-                           cudaStream_t stream, int32_t L = 1)
+                           cudaStream_t stream, int32_t L = 1,
+                           bool host_z = false)
 {
     DevStatus *st = nullptr;
-    gee_status rc =
-        graph_pass_enqueue(ws, graph, Y, L, K, laplacian, Z, &st, stream);
+    gee_status rc = graph_pass_enqueue(ws, graph, Y, L, K, laplacian, Z, &st,
+                                       stream, host_z);
     if (rc != GEE_OK)
         return rc;
     return read_status(st, stream);
@@ -844,7 +921,8 @@ gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
     // checked before any Z row is written, so Z_h stays untouched on error.
     float *Zdirect = mapped_host(Z_h);
     if (Zdirect != nullptr)
-        return embed_graph_dev(ws, graph, Y, K, laplacian, Zdirect, stream);
+        return embed_graph_dev(ws, graph, Y, K, laplacian, Zdirect, stream, 1,
+                               true);
     float *Z = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
     rc = embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);

@@ -551,6 +551,9 @@ struct PullArgs {
     int32_t area_off;     // start of the per-group / per-warp areas
     int32_t group_bytes;  // per group (light) or per warp (heavy)
     int32_t acc_off, slot_off;
+    int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
+                             // k_pull_heavy; 0: every chunk leaves partials
+                             // and k_hub_fixup writes all hub rows
 };
 
 __device__ __forceinline__ void group_sync(int g)
@@ -907,7 +910,8 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
                                  WEIGHTED ? a.val_h + b : nullptr, n, lane,
                                  acc, kHeavyCopies * K + lane, cells);
         __syncwarp();
-        const bool whole = a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
+        const bool whole =
+            a.hub_direct && a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
         float *zrow = a.Z + (int64_t)a.hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
             uint32_t bits;
@@ -933,14 +937,16 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     }
 }
 
-// One warp per hub row cut into several chunks: partials summed in chunk
-// order, then scaled.  Single-chunk rows were written by k_pull_heavy.
+// One warp per hub row: its chunk partials summed in chunk order, then
+// scaled.  Rows with fewer than min_chunks chunks are skipped (1: every hub
+// row; 2: single-chunk rows were written by k_pull_heavy).
 template <bool WEIGHTED>
 __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
                             const int32_t *__restrict__ hub_chunk0,
                             int64_t hubs, const uint32_t *__restrict__ part,
                             const uint32_t *__restrict__ counts, int32_t K,
-                            float *__restrict__ Z, const DevStatus *st)
+                            float *__restrict__ Z, int32_t min_chunks,
+                            const DevStatus *st)
 {
     if (failed(st))
         return;
@@ -949,7 +955,7 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t h = warp; h < hubs; h += nwarps) {
         const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
-        if (c1 - c0 < 2)
+        if (c1 - c0 < min_chunks)
             continue;
         float *zrow = Z + (int64_t)hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
@@ -1155,13 +1161,14 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 
 template <class Kern>
 static cudaError_t launch_persistent(Kern kernel, int threads, size_t smem,
-                                     const PullArgs &a, cudaStream_t stream)
+                                     const PullArgs &a, cudaStream_t stream,
+                                     int ctas = 0)
 {
     cudaError_t e = cudaFuncSetAttribute(
         kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kernel<<<sm_count(), threads, smem, stream>>>(a);
+    kernel<<<ctas > 0 ? ctas : sm_count(), threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1208,7 +1215,7 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream)
+                              cudaStream_t stream, int ctas)
 {
     if (ntiles == 0)
         return cudaSuccess;
@@ -1232,25 +1239,27 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
     const bool w = weighted || laplacian;
     if (L > 1)
         return w ? launch_persistent(k_pull_light<true, true>, threads, smem,
-                                     a, stream)
+                                     a, stream, ctas)
                  : launch_persistent(k_pull_light<false, true>, threads, smem,
-                                     a, stream);
+                                     a, stream, ctas);
     return w ? launch_persistent(k_pull_light<true, false>, threads, smem, a,
-                                 stream)
+                                 stream, ctas)
              : launch_persistent(k_pull_light<false, false>, threads, smem, a,
-                                 stream);
+                                 stream, ctas);
 }
 
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
-                              void *hub_part, const DevStatus *st,
-                              cudaStream_t stream)
+                              void *hub_part, bool partials_only,
+                              const DevStatus *st, cudaStream_t stream,
+                              int ctas)
 {
     if (g.chunks == 0)
         return cudaSuccess;
     PullArgs a = pull_args(g, L, classes, laplacian, nullptr, 0, Yc, counts, Z,
                            hub_part, nullptr, st);
+    a.hub_direct = partials_only ? 0 : 1;
     // kHeavyCopies accumulators of cols cells, then 32 sink cells
     a.group_bytes =
         (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);
@@ -1259,32 +1268,33 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     const bool w = weighted || laplacian;
     if (L > 1)
         return w ? launch_persistent(k_pull_heavy<true, true>, kHeavyThreads,
-                                     smem, a, stream)
+                                     smem, a, stream, ctas)
                  : launch_persistent(k_pull_heavy<false, true>, kHeavyThreads,
-                                     smem, a, stream);
+                                     smem, a, stream, ctas);
     return w ? launch_persistent(k_pull_heavy<true, false>, kHeavyThreads, smem,
-                                 a, stream)
+                                 a, stream, ctas)
              : launch_persistent(k_pull_heavy<false, false>, kHeavyThreads, smem,
-                                 a, stream);
+                                 a, stream, ctas);
 }
 
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
-                             const void *hub_part, const DevStatus *st,
-                             cudaStream_t stream)
+                             const void *hub_part, bool all_rows,
+                             const DevStatus *st, cudaStream_t stream)
 {
     if (g.hubs == 0)
         return cudaSuccess;
     const uint32_t *part = static_cast<const uint32_t *>(hub_part);
     const int fb = grid_for(g.hubs * 32, 256, sm_count() * 8);
+    const int32_t min_chunks = all_rows ? 1 : 2;
     if (weighted || laplacian)
         k_hub_fixup<true><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
                                                   g.hubs, part, counts, K, Z,
-                                                  st);
+                                                  min_chunks, st);
     else
         k_hub_fixup<false><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
                                                    g.hubs, part, counts, K, Z,
-                                                   st);
+                                                   min_chunks, st);
     return cudaGetLastError();
 }
 

@@ -258,22 +258,27 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 // [chunks * K] of 4-byte per-chunk partial sums; work: one 8-byte scratch
 // counter.
 // K arguments of the CSR launches count Z columns (L vectors x classes).
+// ctas: persistent CTAs (0 = one per SM).  partials_only: k_pull_heavy
+// leaves every chunk's sums in hub_part (never writing Z) and
+// launch_hub_fixup(all_rows = true) writes every hub row -- so the two
+// pull kernels may run at the same time on disjoint SMs.
 cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian,
                               const int32_t *tile_row,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream);
+                              cudaStream_t stream, int ctas = 0);
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
-                              void *hub_part, const DevStatus *st,
-                              cudaStream_t stream);
+                              void *hub_part, bool partials_only,
+                              const DevStatus *st, cudaStream_t stream,
+                              int ctas = 0);
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
-                             const void *hub_part, const DevStatus *st,
-                             cudaStream_t stream);
+                             const void *hub_part, bool all_rows,
+                             const DevStatus *st, cudaStream_t stream);
 
 // S4 + S5 (CSR form) for many label vectors (gee_wide.cu): the lanes of a
 // warp take the labels of one arc.  Same order and contract as the three
@@ -349,7 +354,7 @@ bool graph_weighted(const gee_graph *graph);
 gee_status graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                               const int32_t *Y, int32_t L, int32_t K,
                               int32_t laplacian, float *Z, DevStatus **st,
-                              cudaStream_t stream);
+                              cudaStream_t stream, bool host_z = false);
 
 // ------------------------------------------------------------ tracing
 // When tracing is on (gee_profile_enable), a ProfScope brackets one kernel
