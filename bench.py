@@ -67,7 +67,7 @@ WORKLOADS = {
                         "uniform in [2, 64], 30% re-labelings of resident graphs, 80 GiB "
                         "admission budget, host buffers in page-locked memory",
                   pool=64, resident=8, s_lo=1e3, s_hi=1e8, K_lo=2, K_hi=64, relabel=0.3,
-                  load=0.8, budget=80 << 30, streams=4, max_batch=256, seed=5,
+                  load=0.8, budget=80 << 30, streams=8, max_batch=256, seed=5,
                   weighted=False, laplacian=False, scale=0, n=0, s=0, K=0),
     "precision": dict(desc="precision ladder: each arithmetic path (uint32 counts, FP32 weight "
                             "sums, FP32 Laplacian, multi-label and batched forms) against the "
@@ -1019,6 +1019,10 @@ def main():
                     help="shrink the workload by 2^shift (same generator; for profiling)")
     ap.add_argument("--requests", type=int, default=10000,
                     help="serve workload: number of requests")
+    ap.add_argument("--serve-streams", type=int, default=0,
+                    help="serve workload: server slots (0: the workload's)")
+    ap.add_argument("--serve-batch", type=int, default=0,
+                    help="serve workload: requests per group (0: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oneshot", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1027,6 +1031,10 @@ def main():
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     w = dict(WORKLOADS[args.workload])
+    if args.serve_streams:
+        w["streams"] = args.serve_streams
+    if args.serve_batch:
+        w["max_batch"] = args.serve_batch
     if args.scale_shift and "graphs" not in w and "pool" not in w and \
             args.workload not in ("precision", "unsup"):
         sh = args.scale_shift
