@@ -300,7 +300,8 @@ GEE_API gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
  * as one of `streams` slots is free, so work that arrives while other
  * requests run overlaps with them on the GPU:
  *   - consecutive edge-list requests are fused into one gee_embed_batch
- *     launch sequence (up to max_batch requests / max_batch_edges edges);
+ *     launch sequence (up to max_batch requests / max_batch_edges edges),
+ *     replayed as one CUDA graph captured per slot;
  *   - re-labelings of the same resident graph with the same K and variant
  *     waiting anywhere in the queue are fused into one multi-label pass
  *     (W widened to L*K <= GEE_MAX_COLUMNS columns).
@@ -349,6 +350,7 @@ typedef struct gee_server_stats {
     int64_t max_concurrent;    /* most groups in flight at once */
     int64_t resident_bytes;    /* estimated bytes of resident graphs */
     int64_t peak_inflight_bytes;
+    int64_t graph_launches;    /* edge-list groups run as one CUDA graph */
 } gee_server_stats;
 
 /* cfg may be NULL (defaults).  Uses the current CUDA device. */
@@ -373,7 +375,8 @@ GEE_API gee_status gee_server_wait(gee_server *srv, int64_t ticket,
                                    double *latency_ms);
 GEE_API gee_status gee_server_get_stats(gee_server *srv,
                                         gee_server_stats *out);
-/* Finishes every queued request, then releases the server and its graphs. */
+/* Finishes every queued request, then releases the server and its graphs.
+ * Call it after every client thread's gee_server_wait has returned. */
 GEE_API void gee_server_destroy(gee_server *srv);
 
 /*

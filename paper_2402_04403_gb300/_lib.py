@@ -115,7 +115,7 @@ class Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "submitted", "completed", "failed", "groups", "batched_requests", "max_group",
-        "max_concurrent", "resident_bytes", "peak_inflight_bytes")]
+        "max_concurrent", "resident_bytes", "peak_inflight_bytes", "graph_launches")]
 
 
 _lock = threading.Lock()

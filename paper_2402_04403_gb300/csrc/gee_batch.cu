@@ -296,12 +296,13 @@ cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
                           const BatchHeader &hh, bool validate,
                           cudaStream_t stream)
 {
+    (void)hh;
     const int sms = sm_count();
-    const int64_t init_work = hh.count > hh.count_cells ? hh.count : hh.count_cells;
     {
+        // a fixed grid (grid-stride loops) so the sequence's launch
+        // parameters do not depend on the batch
         ProfScope p("k_batch_init", stream);
-        k_batch_init<<<grid_for(init_work, 256, sms * 4), 256, 0, stream>>>(dh,
-                                                                           dP);
+        k_batch_init<<<sms * 4, 256, 0, stream>>>(dh, dP);
     }
     // two CTAs of 512 threads per SM, persistent
     const int blocks = 2 * sms;
@@ -326,6 +327,29 @@ cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
         k_batch_finalize<<<blocks, kBatchThreads, 0, stream>>>(dh, dP);
     }
     return cudaGetLastError();
+}
+
+cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
+                               bool validate, cudaStream_t stream,
+                               cudaGraphExec_t *exec)
+{
+    *exec = nullptr;
+    sm_count();  // cached before the capture
+    cudaError_t e =
+        cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return e;
+    BatchHeader unused{};
+    cudaError_t el = batch_enqueue(dh, dP, unused, validate, stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(stream, &graph);
+    if (el != cudaSuccess)
+        e = el;
+    if (e == cudaSuccess)
+        e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph != nullptr)
+        cudaGraphDestroy(graph);
+    return e;
 }
 
 }  // namespace gee

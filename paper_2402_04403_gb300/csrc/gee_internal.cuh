@@ -334,11 +334,17 @@ struct BatchHeader {
 // (counts_off, yc_off); fills the header's sizes.  Returns yc_bytes.
 int64_t batch_layout(BatchProblem *P, int count, BatchHeader &h);
 // Enqueues the phases (init, labels, [validate,] zero, scatter, finalize)
-// for a header and problem table already in device memory; hh is the host
-// copy of the header (for sizing the init grid).
+// for a header and problem table already in device memory (hh, the host
+// copy of the header, is not needed by the launches).  The launch
+// parameters are only dh and dP, so the sequence can be captured once ...
 cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
                           const BatchHeader &hh, bool validate,
                           cudaStream_t stream);
+// ... into an executable CUDA graph and replayed for every batch whose
+// header and table are written to the same dh and dP.
+cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
+                               bool validate, cudaStream_t stream,
+                               cudaGraphExec_t *exec);
 
 // ------------------------------------------------------------ autotuner
 // The tuned GEE_AUTO choice for an edge-list problem (gee_tune.cu); false

@@ -51,6 +51,11 @@ ProfScope::ProfScope(const char *name, cudaStream_t stream)
 {
     if (!g_on.load(std::memory_order_relaxed))
         return;
+    // launches captured into a CUDA graph are not traced
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream_, &cap) != cudaSuccess ||
+        cap != cudaStreamCaptureStatusNone)
+        return;
     begin_ = take_event();
     if (begin_ != nullptr && cudaEventRecord(begin_, stream_) != cudaSuccess)
         begin_ = nullptr;

@@ -14,7 +14,9 @@
 // A group is enqueued on its slot's stream in full -- host->device copies,
 // kernels, status and Z device->host copies, event -- with its scratch
 // freed stream-ordered behind it, so the thread never waits for the GPU and
-// groups on different slots overlap.  Clients only touch the queue.
+// groups on different slots overlap.  An edge-list group's kernels are one
+// CUDA graph launch: each slot captures the batch sequence once, over its
+// own fixed header and problem table.  Clients only touch the queue.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -64,6 +66,10 @@ struct Slot {
     DevStatus *host_st = nullptr;      // pinned [kMaxBatch]
     BatchProblem *host_tab = nullptr;  // pinned [kMaxBatch]
     BatchHeader *host_hdr = nullptr;   // pinned
+    BatchHeader *dev_hdr = nullptr;    // the batch sequence's header and
+    BatchProblem *dev_tab = nullptr;   // table [kMaxBatch], statuses
+    DevStatus *dev_st = nullptr;       // [kMaxBatch], fixed per slot
+    cudaGraphExec_t batch_graph = nullptr;  // the sequence, captured once
     bool busy = false;
     bool multi = false;                // re-label group
     int64_t n = 0;                     // rows of the re-label group's graph
@@ -164,6 +170,7 @@ void gee_server::complete(Slot &sl)
         for (Req *q : sl.reqs)
             finish(q, sl.launch_error);
     } else if (!sl.multi) {
+        ++stats.graph_launches;
         for (size_t i = 0; i < sl.reqs.size(); ++i)
             finish(sl.reqs[i], static_cast<gee_status>(sl.host_st[i].code));
     } else {
@@ -224,14 +231,13 @@ gee_status gee_server::launch_edges(Slot &sl)
     BatchHeader &hh = *sl.host_hdr;
     hh = BatchHeader{};
     batch_layout(sl.host_tab, count, hh);
-    BatchHeader *dh = nullptr;
-    BatchProblem *dP = nullptr;
-    DevStatus *dst = nullptr;
+    // header, table and statuses live in the slot's fixed buffers, which
+    // the slot's captured batch sequence reads
+    BatchHeader *dh = sl.dev_hdr;
+    BatchProblem *dP = sl.dev_tab;
+    DevStatus *dst = sl.dev_st;
     uint32_t *counts = nullptr;
     uint8_t *Yc = nullptr;
-    GEE_CHECK_CUDA_RET(ws.alloc((void **)&dh, sizeof(BatchHeader)));
-    GEE_CHECK_CUDA_RET(ws.alloc((void **)&dP, sizeof(BatchProblem) * count));
-    GEE_CHECK_CUDA_RET(ws.alloc((void **)&dst, sizeof(DevStatus) * count));
     GEE_CHECK_CUDA_RET(ws.alloc((void **)&counts, sizeof(uint32_t) * hh.count_cells));
     GEE_CHECK_CUDA_RET(ws.alloc((void **)&Yc, (size_t)hh.yc_bytes + 16));
     for (int i = 0; i < count; ++i) {
@@ -246,7 +252,7 @@ gee_status gee_server::launch_edges(Slot &sl)
     GEE_CHECK_CUDA_RET(cudaMemcpyAsync(dP, sl.host_tab,
                                        sizeof(BatchProblem) * count,
                                        cudaMemcpyHostToDevice, st));
-    GEE_CHECK_CUDA_RET(batch_enqueue(dh, dP, hh, true, st));
+    GEE_CHECK_CUDA_RET(cudaGraphLaunch(sl.batch_graph, st));
     GEE_CHECK_CUDA_RET(cudaMemcpyAsync(sl.host_st, dst,
                                        sizeof(DevStatus) * count,
                                        cudaMemcpyDeviceToHost, st));
@@ -484,6 +490,15 @@ gee_status gee_server_create(const gee_server_config *cfg, gee_server **out)
                                sizeof(BatchProblem) * kMaxBatch);
         if (e == cudaSuccess)
             e = cudaMallocHost((void **)&sl.host_hdr, sizeof(BatchHeader));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.dev_hdr, sizeof(BatchHeader));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.dev_tab, sizeof(BatchProblem) * kMaxBatch);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.dev_st, sizeof(DevStatus) * kMaxBatch);
+        if (e == cudaSuccess)
+            e = batch_graph_create(sl.dev_hdr, sl.dev_tab, true, sl.stream,
+                                   &sl.batch_graph);
     }
     if (e != cudaSuccess) {
         gee_server_destroy(srv);
@@ -689,6 +704,14 @@ void gee_server_destroy(gee_server *srv)
             cudaFreeHost(sl.host_tab);
         if (sl.host_hdr != nullptr)
             cudaFreeHost(sl.host_hdr);
+        if (sl.batch_graph != nullptr)
+            cudaGraphExecDestroy(sl.batch_graph);
+        if (sl.dev_hdr != nullptr)
+            cudaFree(sl.dev_hdr);
+        if (sl.dev_tab != nullptr)
+            cudaFree(sl.dev_tab);
+        if (sl.dev_st != nullptr)
+            cudaFree(sl.dev_st);
     }
     if (srv->setup_stream != nullptr)
         cudaStreamDestroy(srv->setup_stream);

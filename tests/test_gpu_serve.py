@@ -89,6 +89,7 @@ def test_mixed_burst_equals_solo_calls(gee, graphs):
         st = srv.stats()
     assert st["completed"] == st["submitted"] == len(reqs) and st["failed"] == 0
     assert st["groups"] < len(reqs) and st["max_group"] >= 12
+    assert st["graph_launches"] >= 1  # edge-list groups ran as CUDA graphs
     with gee.Graph(_dev(eA), nA, weights=_dev(wA)) as GA, gee.Graph(_dev(eB), nB) as GB:
         for kind, args, (Z, lat) in results:
             assert lat > 0
