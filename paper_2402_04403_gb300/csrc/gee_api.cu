@@ -282,7 +282,7 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
     int32_t *tile_row = nullptr;
     void *hub_part = nullptr;
     unsigned long long *work = nullptr;
-    GEE_CHECK_CUDA(ws.alloc((void **)&work, sizeof(unsigned long long)));
+    GEE_CHECK_CUDA(ws.alloc((void **)&work, 2 * sizeof(unsigned long long)));
     GEE_CHECK_CUDA(ws.alloc((void **)&tile_row,
                             sizeof(int32_t) * (ntiles + 1)));
     GEE_CHECK_CUDA(
@@ -299,8 +299,9 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         {
             ProfScope p("k_pull_heavy", side.stream());
             GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
-                                             counts, Z, hub_part, true, st,
-                                             side.stream(), sms - light_ctas));
+                                             counts, Z, hub_part, true, work + 1,
+                                             st, side.stream(),
+                                             sms - light_ctas));
         }
         {
             ProfScope p("k_pull_light", stream);
@@ -326,8 +327,8 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
     if (g.chunks > 0) {
         ProfScope p("k_pull_heavy", stream);
         GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
-                                         counts, Z, hub_part, false, st,
-                                         stream));
+                                         counts, Z, hub_part, false, work + 1,
+                                         st, stream));
     }
     if (g.hubs > 0) {
         ProfScope p("k_hub_fixup", stream);

@@ -510,8 +510,9 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 //   once with 16-byte stores.
 //   Rows kept in the hub CSR have no arcs here and get zeros.
 // k_pull_heavy: rows with more than kHubDegree arcs, cut into chunks of at
-//   most kHubChunk arcs.  One warp per chunk, no block barriers; warps take
-//   contiguous chunk ranges of equal arc counts.  A single-chunk row's Z row
+//   most kHubChunk arcs.  One warp per chunk, no block barriers; warps draw
+//   kChunkGrab consecutive chunks at a time from a counter (measured faster
+//   than fixed ranges of equal arc counts: no tail of idle warps).  A single-chunk row's Z row
 //   is written directly, overwriting the zeros of k_pull_light (which runs
 //   first); longer rows leave per-chunk partial sums for k_hub_fixup.
 constexpr int kGroupThreads = 128;
@@ -520,6 +521,7 @@ constexpr int kUnroll = 8;        // arcs in flight per thread
 constexpr int kTableCounts = 8;   // counts below this convert by table
 constexpr int kHeavyThreads = 1024;
 constexpr int kHeavyCopies = 1;   // per-warp accumulator copies
+constexpr int kChunkGrab = 4;     // hub chunks a warp draws at a time
 
 struct PullArgs {
     const int64_t *rowptr;
@@ -879,24 +881,17 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     uint32_t *acc = reinterpret_cast<uint32_t *>(sm + a.area_off +
                                                  (size_t)wib * a.group_bytes);
     float *accf = reinterpret_cast<float *>(acc);
-    // this warp's chunks: those whose first arc lies in its equal share of
-    // the hub arcs (chunk_begin is increasing)
-    const int64_t nw = (int64_t)gridDim.x * (kHeavyThreads / 32);
-    const int64_t w = (int64_t)blockIdx.x * (kHeavyThreads / 32) + wib;
-    auto first_chunk_at = [&](int64_t arc) {
-        int64_t lo = 0, hi = a.chunks;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (a.chunk_begin[mid] < arc)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        return lo;
-    };
-    const int64_t c_lo = first_chunk_at(a.hub_arcs * w / nw);
-    const int64_t c_hi = first_chunk_at(a.hub_arcs * (w + 1) / nw);
     const int copy = (lane & (kHeavyCopies - 1)) * K;
+    // warps draw kChunkGrab consecutive chunks at a time from a counter
+    for (;;) {
+        unsigned long long g0 = 0;
+        if (lane == 0)
+            g0 = atomicAdd(a.work, (unsigned long long)kChunkGrab);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        if (g0 >= (unsigned long long)a.chunks)
+            break;
+        const int64_t c_lo = (int64_t)g0;
+        const int64_t c_hi = min(c_lo + kChunkGrab, a.chunks);
     for (int64_t c = c_lo; c < c_hi; ++c) {
         for (int i = lane; i < kHeavyCopies * K; i += 32)
             acc[i] = 0u;
@@ -934,6 +929,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
                 a.hub_part[c * K + k] = bits;
         }
         __syncwarp();
+    }
     }
 }
 
@@ -1252,14 +1248,17 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               void *hub_part, bool partials_only,
-                              const DevStatus *st, cudaStream_t stream,
-                              int ctas)
+                              unsigned long long *work, const DevStatus *st,
+                              cudaStream_t stream, int ctas)
 {
     if (g.chunks == 0)
         return cudaSuccess;
     PullArgs a = pull_args(g, L, classes, laplacian, nullptr, 0, Yc, counts, Z,
-                           hub_part, nullptr, st);
+                           hub_part, work, st);
     a.hub_direct = partials_only ? 0 : 1;
+    cudaError_t e0 = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
+    if (e0 != cudaSuccess)
+        return e0;
     // kHeavyCopies accumulators of cols cells, then 32 sink cells
     a.group_bytes =
         (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);

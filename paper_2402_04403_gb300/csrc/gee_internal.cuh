@@ -255,8 +255,8 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 // light rows (every Z row of the tile range; hub rows get zeros), hub-row
 // chunks (single-chunk hub rows written directly) and the fixup of hub rows
 // with several chunks.  Yc is in rank order.  hub_part: scratch
-// [chunks * K] of 4-byte per-chunk partial sums; work: one 8-byte scratch
-// counter.
+// [chunks * K] of 4-byte per-chunk partial sums; work: an 8-byte scratch
+// counter per launch (the light and the heavy launch each need their own).
 // K arguments of the CSR launches count Z columns (L vectors x classes).
 // ctas: persistent CTAs (0 = one per SM).  partials_only: k_pull_heavy
 // leaves every chunk's sums in hub_part (never writing Z) and
@@ -273,8 +273,8 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               void *hub_part, bool partials_only,
-                              const DevStatus *st, cudaStream_t stream,
-                              int ctas = 0);
+                              unsigned long long *work, const DevStatus *st,
+                              cudaStream_t stream, int ctas = 0);
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
                              const void *hub_part, bool all_rows,
