@@ -763,46 +763,59 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
     }
 }
 
-template <bool WEIGHTED, bool MULTI>
+// Row starts of a tile, loaded ahead into registers: entry i = gt + j*128
+// of rowptr[r0 .. r1] for the thread with group rank gt.
+constexpr int kRowsAhead = 3;  // (4,096 / 16 + 1) row starts over 128 threads
+struct TileRows {
+    int32_t r0 = 0, r1 = 0;
+    int64_t A0 = 0;
+    int64_t rv[kRowsAhead];
+};
+
+__device__ __forceinline__ void load_tile_rows(const PullArgs &a, int gt,
+                                               TileRows &tr)
+{
+    tr.A0 = a.rowptr[tr.r0];
+    const int NR = tr.r1 - tr.r0;
+#pragma unroll
+    for (int j = 0; j < kRowsAhead; ++j) {
+        const int i = gt + j * kGroupThreads;
+        tr.rv[j] = i <= NR ? a.rowptr[tr.r0 + i] : 0;
+    }
+}
+
+// One row tile (after the setup has been published by the caller's
+// barrier): sweep its arcs into the accumulators, barrier, then scale and
+// write its Z rows.  `before_write` runs between the barrier and the write
+// phase (the caller issues the next tile's loads there).
+template <bool WEIGHTED, bool MULTI, class BeforeWrite>
 __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                                          unsigned char *gs,
                                          const uint32_t *nk,
-                                         const float *table, int64_t t)
+                                         const float *table,
+                                         const TileRows &tr,
+                                         BeforeWrite &&before_write)
 {
     const int32_t K = a.cols;  // cells per row
-    const int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
-    if (r0 == r1)
-        return;
-    const int NR = r1 - r0;
+    const int NR = tr.r1 - tr.r0;
     int32_t *rp = reinterpret_cast<int32_t *>(gs);  // row starts, tile-relative
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
-
-    const int64_t g0 = (int64_t)r0 * K;  // first Z cell of the tile
+    const int64_t g0 = (int64_t)tr.r0 * K;  // first Z cell of the tile
     // acc[off + j] holds cell g0 + j, off = the cell's float offset within
     // its 16-byte block of Z (any 4-byte aligned Z)
     const int off = (int)((reinterpret_cast<uintptr_t>(a.Z + g0) >> 2) & 3);
     const int cells = NR * K;
-
-    // setup: zero the accumulators, load the tile's row starts
-    {
-        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
-            acc4[c] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    const int64_t A0 = a.rowptr[r0];
-    for (int i = gt; i <= NR; i += kGroupThreads)
-        rp[i] = (int32_t)(a.rowptr[r0 + i] - A0);
-    group_sync(g);
-    const int NA = rp[NR];
+    const int NA = NR > 0 ? rp[NR] : 0;
 
     // sweep: the row of arc i is the last row starting at or before i
     if (NA > 0) {
-        TileCells cells{rp, NR, K, off, 0, 0};
+        TileCells tc{rp, NR, K, off, 0, 0};
         sweep_arcs<WEIGHTED, MULTI, kGroupThreads>(
-            a, a.col + A0, WEIGHTED ? a.val + A0 : nullptr, NA, gt, acc,
-            a.max_rows * K + 8 + (gt & 31), cells);
+            a, a.col + tr.A0, WEIGHTED ? a.val + tr.A0 : nullptr, NA, gt, acc,
+            a.max_rows * K + 8 + (gt & 31), tc);
     }
     group_sync(g);
+    before_write();
 
     // the tile's rows are contiguous in Z: scale once and stream out with
     // 16-byte stores between an unaligned head and tail; all-zero quads
@@ -839,6 +852,11 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     }
 }
 
+// Each group pipelines its tiles: it draws tile t+1 before the setup
+// barrier of tile t, loads t+1's row range while sweeping t and t+1's row
+// starts while writing t, so a tile's setup finds its row starts in
+// registers.  Three group barriers per tile: setup published, accumulators
+// complete, accumulators free again.
 template <bool WEIGHTED, bool MULTI>
 __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     k_pull_light(PullArgs a)
@@ -854,14 +872,54 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     const int gt = threadIdx.x - g * kGroupThreads;
     unsigned char *gs = sm + a.area_off + (size_t)g * a.group_bytes;
     long long *slot = reinterpret_cast<long long *>(gs + a.slot_off);
-    for (int it = 0;; ++it) {
+    int32_t *rp = reinterpret_cast<int32_t *>(gs);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
+    const int32_t K = a.cols;
+
+    if (gt == 0)
+        slot[0] = (long long)atomicAdd(a.work, 1ull);
+    group_sync(g);
+    int64_t item = slot[0];
+    TileRows cur;
+    if (item < a.ntiles) {
+        cur.r0 = a.tile_row[item];
+        cur.r1 = a.tile_row[item + 1];
+        load_tile_rows(a, gt, cur);
+    }
+    for (int it = 0; item < a.ntiles; ++it) {
+        // the next tile, read by the group after the setup barrier below
         if (gt == 0)
-            slot[it & 1] = (long long)atomicAdd(a.work, 1ull);
+            slot[(it + 1) & 1] = (long long)atomicAdd(a.work, 1ull);
+        // setup: zero the accumulators, publish the row starts
+        const int NR = cur.r1 - cur.r0;
+        const int cells = NR * K;
+        const int off = (int)((reinterpret_cast<uintptr_t>(
+                                   a.Z + (int64_t)cur.r0 * K) >> 2) & 3);
+        {
+            uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+            for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
+                acc4[c] = make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < kRowsAhead; ++j) {
+            const int i = gt + j * kGroupThreads;
+            if (i <= NR)
+                rp[i] = (int32_t)(cur.rv[j] - cur.A0);
+        }
         group_sync(g);
-        const int64_t item = slot[it & 1];
-        if (item >= a.ntiles)
-            break;
-        row_tile<WEIGHTED, MULTI>(a, g, gt, gs, nk, table, item);
+        const int64_t next = slot[(it + 1) & 1];
+        TileRows nxt;
+        if (next < a.ntiles) {  // in flight during the sweep
+            nxt.r0 = a.tile_row[next];
+            nxt.r1 = a.tile_row[next + 1];
+        }
+        row_tile<WEIGHTED, MULTI>(a, g, gt, gs, nk, table, cur, [&]() {
+            if (next < a.ntiles)  // in flight during the write phase
+                load_tile_rows(a, gt, nxt);
+        });
+        group_sync(g);
+        item = next;
+        cur = nxt;
     }
 }
 
