@@ -81,9 +81,12 @@ typedef enum gee_status {
     GEE_ERR_UNSUPPORTED = 8   /* e.g. K > GEE_MAX_CLASSES */
 } gee_status;
 
-/* Edge-pass strategy.  AUTO picks PRIVATE when n*K fits in shared memory and
- * ATOMIC otherwise; SEGMENTED (CSR by row, each Z row written once, no global
- * atomics) is what a gee_graph always uses. */
+/* Edge-pass strategy of the edge-list entry points.  AUTO takes the choice
+ * gee_autotune measured for the nearest problem shape when the device has a
+ * tuning table, else PRIVATE when n*K fits in shared memory and every CTA
+ * would merge several edges per cell, ATOMIC otherwise.  SEGMENTED (CSR by
+ * row, each Z row written once, no global atomics) is what a gee_graph
+ * always uses. */
 typedef enum gee_strategy {
     GEE_AUTO = 0,
     GEE_ATOMIC = 1,    /* edge stream, red.global atomics into Z */
@@ -122,7 +125,12 @@ GEE_API gee_status gee_histogram(const int32_t *Y, int64_t n, int32_t K,
 
 /*
  * Z = A W for an edge list (Alg. 1 / Alg. 2 of the paper): one call from
- * edges and labels to the embedding.  opts may be NULL (defaults).
+ * edges and labels to the embedding.  edges: device int32 [s][2]; weights:
+ * device float [s] or NULL; Y: device int32 [n]; Z: device float [n][K],
+ * written in full (caller-owned).  opts may be NULL (defaults).  Errors:
+ * GEE_ERR_LABEL_RANGE / GEE_ERR_NODE_RANGE before Z is touched (see
+ * validate_edges), GEE_ERR_INVALID_ARG for a negative weight with the
+ * Laplacian variant, GEE_ERR_OOM when the scratch does not fit.
  */
 GEE_API gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
                      const int32_t *Y, int64_t n, int32_t K, int32_t laplacian,
@@ -152,7 +160,11 @@ GEE_API gee_status gee_graph_create(const int32_t *edges, const float *weights,
                             int64_t s, int64_t n, gee_stream_t stream,
                             gee_graph **out);
 
-/* Z = A W for a resident graph and a label vector Y (device int32 [n]). */
+/* Z = A W for a resident graph and a label vector: Y device int32 [n],
+ * Z device float [n][K] written in full, n the graph's.  Unit-weight
+ * graphs give the bit-exact counts result.  opts is accepted for symmetry
+ * (the resident pass has no strategy choice).  Calls on different streams
+ * may use one graph at the same time. */
 GEE_API gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
                            int32_t laplacian, float *Z,
                            const gee_options *opts, gee_stream_t stream);
