@@ -499,8 +499,10 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 // ------------------------------------------------------------ pull
 // Two persistent kernels, one CTA per SM.  Labels are read through the
 // read-only path: with targets stored as degree ranks the most referenced
-// labels are the first bytes of Yc and stay in L1 (measured faster than
-// copying them into shared memory, which also costs the L1 capacity).
+// labels are the first bytes of Yc and stay in L1.  The hub-row kernel,
+// bound by its L1 sector lookups, also keeps the labels of the first
+// kHotLabels ranks in shared memory (128 K measured best: larger copies
+// shrink L1 too much; the row-tile kernel has no shared memory to spare).
 //
 // k_pull_light: rows with at most kHubDegree arcs.  NG independent groups of
 //   128 threads (own named barrier each) take row tiles from a global
@@ -522,6 +524,7 @@ constexpr int kTableCounts = 8;   // counts below this convert by table
 constexpr int kHeavyThreads = 1024;
 constexpr int kHeavyCopies = 1;   // per-warp accumulator copies
 constexpr int kChunkGrab = 4;     // hub chunks a warp draws at a time
+constexpr int kHotLabels = 131072; // hub-row kernel: labels kept in shared memory
 
 struct PullArgs {
     const int64_t *rowptr;
@@ -553,6 +556,8 @@ struct PullArgs {
     int32_t area_off;     // start of the per-group / per-warp areas
     int32_t group_bytes;  // per group (light) or per warp (heavy)
     int32_t acc_off, slot_off;
+    int32_t hot_off, hot_n;  // heavy kernel: shared copy of the labels of
+                             // ranks [0, hot_n), a multiple of 16
     int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
                              // k_pull_heavy; 0: every chunk leaves partials
                              // and k_hub_fixup writes all hub rows
@@ -656,7 +661,9 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            const int32_t *colp,
                                            const float *valp, int NA, int t,
                                            uint32_t *acc, int sink,
-                                           Cells &cells)
+                                           Cells &cells,
+                                           const uint8_t *hot = nullptr,
+                                           int hot_n = 0)
 {
     float *accf = reinterpret_cast<float *>(acc);
     auto put = [&](int c, float w) {
@@ -698,8 +705,12 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
             }
         }
     };
+    // the labels of the hot_n most referenced ranks come from the CTA's
+    // shared-memory copy, the rest through L1
     auto fetch = [&](int32_t v) -> uint32_t {
-        return MULTI ? (uint32_t)v : label_of(a, v);
+        if (MULTI)
+            return (uint32_t)v;
+        return v < hot_n ? (uint32_t)hot[v] : label_of(a, v);
     };
     const int head =
         min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
@@ -932,6 +943,12 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     uint32_t *nk = reinterpret_cast<uint32_t *>(sm);
     float *table = reinterpret_cast<float *>(sm + ((a.cols * 4 + 15) & ~15));
     load_shared<WEIGHTED>(a, nk, table);
+    // copy of the labels of the most referenced ranks (front of Yc)
+    uint8_t *hot = sm + a.hot_off;
+    const int hot_n = MULTI ? 0 : a.hot_n;
+    for (int i = threadIdx.x; i < hot_n / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(hot)[i] =
+            __ldg(reinterpret_cast<const uint4 *>(a.Yc) + i);
     __syncthreads();
     const int32_t K = a.cols;  // cells per row
     const int lane = threadIdx.x & 31;
@@ -961,7 +978,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         ChunkCells cells{copy};
         sweep_arcs<WEIGHTED, MULTI, 32>(a, a.col_h + b,
                                  WEIGHTED ? a.val_h + b : nullptr, n, lane,
-                                 acc, kHeavyCopies * K + lane, cells);
+                                 acc, kHeavyCopies * K + lane, cells, hot, hot_n);
         __syncwarp();
         const bool whole =
             a.hub_direct && a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
@@ -1317,11 +1334,14 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     cudaError_t e0 = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e0 != cudaSuccess)
         return e0;
-    // kHeavyCopies accumulators of cols cells, then 32 sink cells
+    // kHeavyCopies accumulators of cols cells, then 32 sink cells, then the
+    // hot labels (at most the first n ranks, a multiple of 16 bytes)
     a.group_bytes =
         (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);
-    const size_t smem =
-        plan_shared((size_t)(kHeavyThreads / 32) * a.group_bytes, a);
+    a.hot_n = L > 1 ? 0 : (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
+    const size_t area = (size_t)(kHeavyThreads / 32) * a.group_bytes;
+    const size_t smem = plan_shared(area + (size_t)a.hot_n, a);
+    a.hot_off = a.area_off + (int32_t)area;
     const bool w = weighted || laplacian;
     if (L > 1)
         return w ? launch_persistent(k_pull_heavy<true, true>, kHeavyThreads,
