@@ -61,6 +61,22 @@ cudaError_t device_pool(cudaMemPool_t *out)
     return cudaSuccess;
 }
 
+// Device address of page-locked (registered or cudaMallocHost) host memory,
+// or null for pageable or unaligned memory.
+float *mapped_host(float *p)
+{
+    if (p == nullptr || (reinterpret_cast<uintptr_t>(p) & 3) != 0)
+        return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory may report an error: clear it
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr)
+        return nullptr;
+    return static_cast<float *>(at.devicePointer);
+}
+
 namespace {
 
 // Long-lived arrays of a resident graph.
@@ -130,22 +146,6 @@ inline bool words_misaligned(const void *a, const void *b = nullptr,
 {
     return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
              reinterpret_cast<uintptr_t>(c)) & 3) != 0;
-}
-
-// Device address of page-locked (registered or cudaMallocHost) host memory,
-// or null for pageable or unaligned memory.
-float *mapped_host(float *p)
-{
-    if (p == nullptr || (reinterpret_cast<uintptr_t>(p) & 3) != 0)
-        return nullptr;
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();  // pageable memory may report an error: clear it
-        return nullptr;
-    }
-    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr)
-        return nullptr;
-    return static_cast<float *>(at.devicePointer);
 }
 
 #define GEE_CHECK_CUDA(x)                                                      \

@@ -199,6 +199,10 @@ gee_status from_cuda(cudaError_t e);
 // back to the driver.
 cudaError_t device_pool(cudaMemPool_t *out);
 
+// Device address of page-locked (registered or cudaMallocHost) host memory,
+// or null for pageable or unaligned memory.
+float *mapped_host(float *p);
+
 // Scratch of one call: stream-ordered allocations, released (to the pool) on
 // the same stream when the Workspace is destroyed -- after the work enqueued
 // before, so a Workspace may go out of scope as soon as its work is queued.

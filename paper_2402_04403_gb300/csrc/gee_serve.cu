@@ -12,7 +12,8 @@
 //                          K and variant
 //   3. sleeps until a submission or a poll interval passes.
 // A group is enqueued on its slot's stream in full -- host->device copies,
-// kernels, status and Z device->host copies, event -- with its scratch
+// kernels, status and Z back to the host (copies, or a split kernel that
+// writes page-locked targets of a multi-label pass), event -- with its scratch
 // freed stream-ordered behind it, so the thread never waits for the GPU and
 // groups on different slots overlap.  An edge-list group's kernels are one
 // CUDA graph launch: each slot captures the batch sequence once, over its
@@ -66,6 +67,7 @@ struct Slot {
     DevStatus *host_st = nullptr;      // pinned [kMaxBatch]
     BatchProblem *host_tab = nullptr;  // pinned [kMaxBatch]
     BatchHeader *host_hdr = nullptr;   // pinned
+    float **host_dst = nullptr;        // pinned [kMaxBatch]: split targets
     BatchHeader *dev_hdr = nullptr;    // the batch sequence's header and
     BatchProblem *dev_tab = nullptr;   // table [kMaxBatch], statuses
     DevStatus *dev_st = nullptr;       // [kMaxBatch], fixed per slot
@@ -79,6 +81,79 @@ struct Slot {
 };
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
+
+// Copies column block l of a multi-label Z (n rows of L*K floats, vector l
+// in columns [l*K, (l+1)*K)) to dst[l] (n rows of K floats), one grid row
+// per vector; a null dst[l] is skipped.  The targets are page-locked host
+// buffers seen through their device addresses, so every store crosses the
+// host link, whose rate depends on whole 128-byte lines and on the stores in
+// flight: up to 31 leading scalars bring a target to a line boundary, the
+// body goes out as 16-byte stores, and each thread loads four of them before
+// it stores any.  A strided device-to-host copy with rows this short (K*4
+// bytes) moves a fraction of the link rate.
+constexpr int kSplitThreads = 256;
+constexpr int kSplitQuads = 4;
+constexpr int kSplitBlocks = 64;  // in all; enough for the link, few SMs
+
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_vectors(const float *__restrict__ Z, int64_t n, int32_t L, int32_t K,
+                float *const *__restrict__ dst)
+{
+    float *d = dst[blockIdx.y];
+    if (d == nullptr)
+        return;
+    const int64_t cells = n * K;
+    const int64_t LK = (int64_t)L * K;
+    const int64_t col0 = (int64_t)blockIdx.y * K;
+    const auto src = [&](int64_t c) {
+        const int64_t u = c / K;
+        return __ldg(Z + u * LK + col0 + (c - u * K));
+    };
+    // d is 4-byte aligned: head = floats up to the next 128-byte line
+    int64_t head =
+        (int64_t)(((128u - (uint32_t)(reinterpret_cast<uintptr_t>(d) & 127u)) &
+                   127u) >> 2);
+    if (head > cells)
+        head = cells;
+    const int64_t quads = (cells - head) >> 2;
+    const int64_t tail0 = head + quads * 4;
+    if (blockIdx.x == 0) {
+        const int64_t t = threadIdx.x;
+        if (t < head)
+            d[t] = src(t);
+        if (t < cells - tail0)
+            d[tail0 + t] = src(tail0 + t);
+    }
+    float4 *dq = reinterpret_cast<float4 *>(d + head);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+         q0 < quads; q0 += stride * kSplitQuads) {
+        float v[kSplitQuads][4];
+#pragma unroll
+        for (int j = 0; j < kSplitQuads; ++j) {
+            const int64_t q = q0 + j * stride;
+            if (q < quads) {
+                const int64_t c = head + q * 4;
+                int64_t u = c / K;
+                int32_t k = (int32_t)(c - u * K);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    v[j][e] = __ldg(Z + u * LK + col0 + k);
+                    if (++k == K) {
+                        k = 0;
+                        ++u;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kSplitQuads; ++j) {
+            const int64_t q = q0 + j * stride;
+            if (q < quads)
+                dq[q] = make_float4(v[j][0], v[j][1], v[j][2], v[j][3]);
+        }
+    }
+}
 
 #define GEE_CHECK_CUDA_RET(x)                                                  \
     do {                                                                       \
@@ -290,16 +365,37 @@ gee_status gee_server::launch_relabel(Slot &sl, GraphEntry &ge)
         return rc;
     GEE_CHECK_CUDA_RET(cudaMemcpyAsync(sl.host_st, dst, sizeof(DevStatus),
                                        cudaMemcpyDeviceToHost, st));
-    for (int32_t l = 0; l < L && n > 0; ++l) {
-        float *out = sl.reqs[(size_t)l]->r.Z_h;
-        if (L == 1)
-            GEE_CHECK_CUDA_RET(cudaMemcpyAsync(out, Z, (size_t)(n * K) * 4,
-                                               cudaMemcpyDeviceToHost, st));
-        else
-            GEE_CHECK_CUDA_RET(cudaMemcpy2DAsync(
-                out, (size_t)K * 4, Z + (size_t)l * K, (size_t)L * K * 4,
-                (size_t)K * 4, (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (n == 0)
+        return GEE_OK;
+    if (L == 1) {
+        GEE_CHECK_CUDA_RET(cudaMemcpyAsync(sl.reqs[0]->r.Z_h, Z,
+                                           (size_t)(n * K) * 4,
+                                           cudaMemcpyDeviceToHost, st));
+        return GEE_OK;
     }
+    // page-locked targets: one split kernel writes them over the link;
+    // pageable ones: a strided copy each
+    int32_t mapped = 0;
+    for (int32_t l = 0; l < L; ++l) {
+        sl.host_dst[l] = mapped_host(sl.reqs[(size_t)l]->r.Z_h);
+        mapped += sl.host_dst[l] != nullptr ? 1 : 0;
+    }
+    if (mapped > 0) {
+        float **dtab = nullptr;
+        GEE_CHECK_CUDA_RET(ws.alloc((void **)&dtab, sizeof(float *) * L));
+        GEE_CHECK_CUDA_RET(cudaMemcpyAsync(dtab, sl.host_dst,
+                                           sizeof(float *) * L,
+                                           cudaMemcpyHostToDevice, st));
+        const dim3 grid((unsigned)((kSplitBlocks + L - 1) / L), (unsigned)L);
+        k_split_vectors<<<grid, kSplitThreads, 0, st>>>(Z, n, L, K, dtab);
+        GEE_CHECK_CUDA_RET(cudaGetLastError());
+    }
+    for (int32_t l = 0; l < L; ++l)
+        if (sl.host_dst[l] == nullptr)
+            GEE_CHECK_CUDA_RET(cudaMemcpy2DAsync(
+                sl.reqs[(size_t)l]->r.Z_h, (size_t)K * 4, Z + (size_t)l * K,
+                (size_t)L * K * 4, (size_t)K * 4, (size_t)n,
+                cudaMemcpyDeviceToHost, st));
     return GEE_OK;
 }
 
@@ -490,6 +586,8 @@ gee_status gee_server_create(const gee_server_config *cfg, gee_server **out)
                                sizeof(BatchProblem) * kMaxBatch);
         if (e == cudaSuccess)
             e = cudaMallocHost((void **)&sl.host_hdr, sizeof(BatchHeader));
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&sl.host_dst, sizeof(float *) * kMaxBatch);
         if (e == cudaSuccess)
             e = cudaMalloc((void **)&sl.dev_hdr, sizeof(BatchHeader));
         if (e == cudaSuccess)
@@ -704,6 +802,8 @@ void gee_server_destroy(gee_server *srv)
             cudaFreeHost(sl.host_tab);
         if (sl.host_hdr != nullptr)
             cudaFreeHost(sl.host_hdr);
+        if (sl.host_dst != nullptr)
+            cudaFreeHost(sl.host_dst);
         if (sl.batch_graph != nullptr)
             cudaGraphExecDestroy(sl.batch_graph);
         if (sl.dev_hdr != nullptr)

@@ -197,3 +197,46 @@ def test_bad_label_fails_only_its_request(gee, graphs):
         srv.drop_graph(gB)
         with pytest.raises(gee.GeeError):
             srv.submit(Ys[0], 5, graph=gB)
+
+
+def test_multi_group_outputs_page_locked_and_pageable(gee, graphs):
+    """A fused multi-label group returns each vector's columns to that
+    request's own output: page-locked outputs (placed so that no two start at
+    the same offset within a 128-byte line) are written over the host link by
+    the split kernel, a pageable one by a strided copy.  Every output equals
+    the oracle and no float around the outputs changes."""
+    import torch
+    (eB, _, nB) = graphs[1]
+    cases = ((9, 12), (5, 3), (64, 16))  # (K, L): wide and narrow forms; 16 x 64 = 1,024
+    with gee.Server(streams=1) as srv:
+        gB = srv.add_graph(eB, nB)
+        # hold the only slot so the re-labelings queue up and group
+        e = graphgen.random_graph(50000, 2_000_000, seed=2)
+        Yb = graphgen.labels(50000, 3, seed=2)
+        for K, L in cases:
+            Ys = [graphgen.labels(nB, K, seed=900 + 37 * K + l, frac_unlabeled=0.1)
+                  for l in range(L)]
+            gaps = [1 + 7 * l for l in range(L)]  # floats before each output
+            total = sum(gaps) + L * nB * K + 32
+            buf = torch.full((total,), float("nan"), dtype=torch.float32, pin_memory=True)
+            flat = buf.numpy()
+            outs, spans, pos = [], [], 0
+            for l in range(L):
+                pos += gaps[l]
+                if l == 1:
+                    outs.append(np.empty((nB, K), np.float32))  # pageable
+                else:
+                    outs.append(flat[pos:pos + nB * K].reshape(nB, K))
+                    spans.append((pos, pos + nB * K))
+                pos += nB * K
+            first = srv.submit(Yb, 3, edges=e)
+            tickets = [srv.submit(Y, K, graph=gB, out=o) for Y, o in zip(Ys, outs)]
+            srv.wait(first)
+            for l, (Y, t) in enumerate(zip(Ys, tickets)):
+                srv.wait(t)
+                assert np.array_equal(outs[l], oracle.embed_counts32(eB, Y, K)), (K, L, l)
+            outside = np.ones(total, bool)
+            for a, b in spans:
+                outside[a:b] = False
+            assert np.all(np.isnan(flat[outside])), (K, L)
+        assert srv.stats()["max_group"] == 16
