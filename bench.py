@@ -522,6 +522,35 @@ def run_batch(args, w, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def _host_link_rates(dev, nbytes=1 << 30, reps=3):
+    """Copy-engine rates between page-locked host memory and the device
+    (GB/s): each direction alone, and both at once on two streams."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_out = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(up, down):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if up:
+                with torch.cuda.stream(s1):
+                    d_in.copy_(h_in, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            best = min(best, time.perf_counter() - t0)
+        return (int(up) + int(down)) * nbytes / best / 1e9
+
+    return {"h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True),
+            "both_gbs": timed(True, True), "probe_bytes": nbytes}
+
+
 def run_serve(args, w, world, rank, local):
     """Serving (gee_server_*): a burst of all requests for the server's
     throughput, then a Poisson stream at `load` x the plain path's capacity
@@ -665,6 +694,13 @@ def run_serve(args, w, world, rank, local):
         finish = start + service[i]
         plain_lat[i] = (finish - arrivals[i]) * 1e3
     pct = lambda a, q: float(np.percentile(a, q))
+    # bytes the burst moves over the host link (edges and labels in, Z out)
+    h2d = sum((0 if kinds[i] else 8 * pool[g]["s"]) + 4 * pool[g]["n"]
+              for i, (g, _) in enumerate(picks))
+    d2h = sum(4 * pool[g]["n"] * pool[g]["labs"][j][0] for g, j in picks)
+    link = _host_link_rates(dev)
+    floor_s = max(h2d / (link["h2d_gbs"] * 1e9), d2h / (link["d2h_gbs"] * 1e9),
+                  (h2d + d2h) / (link["both_gbs"] * 1e9))
     line = {
         "metric": "serving: edges/s and p50/p99 latency vs sequential plain calls",
         "value": world * total_edges / burst_s, "unit": "edges/s", "n_gpus": world,
@@ -685,6 +721,10 @@ def run_serve(args, w, world, rank, local):
                    "p50_ms_plain_same_arrivals": pct(plain_lat, 50),
                    "p99_ms_plain_same_arrivals": pct(plain_lat, 99)},
         "speedup_vs_plain": plain_total / burst_s,
+        "e2e": {"value": world * total_edges / burst_s, "unit": "edges/s",
+                "h2d_bytes_per_step": h2d / R, "d2h_bytes_per_step": d2h / R},
+        "host_link": dict(link, h2d_bytes=h2d, d2h_bytes=d2h, floor_seconds=floor_s,
+                          burst_frac_of_floor=floor_s / burst_s),
         "max_abs_diff_vs_plain": worst,
         "server_stats": {"burst": st_burst, "end": st},
         "clocks": clocks,

@@ -499,10 +499,16 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 // ------------------------------------------------------------ pull
 // Two persistent kernels, one CTA per SM.  Labels are read through the
 // read-only path: with targets stored as degree ranks the most referenced
-// labels are the first bytes of Yc and stay in L1.  The hub-row kernel,
-// bound by its L1 sector lookups, also keeps the labels of the first
-// kHotLabels ranks in shared memory (128 K measured best: larger copies
-// shrink L1 too much; the row-tile kernel has no shared memory to spare).
+// labels are the first bytes of Yc and stay in L1.  A random byte gather
+// that misses L1 costs about one SM clock in the L1 unit whatever its form,
+// so the hub-row kernel, bound by those gathers, keeps the labels of the
+// first kHotLabels ranks in shared memory (128 K measured best: larger
+// copies shrink L1 too much; the row-tile kernel has no shared memory to
+// spare).  Labels of the remaining ranks (hub rows), or of ranks from
+// kLightColdFrom on (row tiles), almost never hit L1 and are read from L2
+// without taking an L1 line, which leaves the lines to the loads in flight
+// (hub rows 6.97 -> 6.41 ms, row tiles 5.47 -> 5.34 ms on the paper-scale
+// graph).
 //
 // k_pull_light: rows with at most kHubDegree arcs.  NG independent groups of
 //   128 threads (own named barrier each) take row tiles from a global
@@ -525,6 +531,7 @@ constexpr int kHeavyThreads = 1024;
 constexpr int kHeavyCopies = 1;   // per-warp accumulator copies
 constexpr int kChunkGrab = 4;     // hub chunks a warp draws at a time
 constexpr int kHotLabels = 131072; // hub-row kernel: labels kept in shared memory
+constexpr int kLightColdFrom = 1 << 18;  // row-tile kernel: ranks read past L1
 
 struct PullArgs {
     const int64_t *rowptr;
@@ -558,6 +565,7 @@ struct PullArgs {
     int32_t acc_off, slot_off;
     int32_t hot_off, hot_n;  // heavy kernel: shared copy of the labels of
                              // ranks [0, hot_n), a multiple of 16
+    int32_t cold_from;       // labels of ranks >= cold_from are read past L1
     int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
                              // k_pull_heavy; 0: every chunk leaves partials
                              // and k_hub_fixup writes all hub rows
@@ -573,6 +581,16 @@ __device__ __forceinline__ void group_sync(int g)
 __device__ __forceinline__ uint32_t label_of(const PullArgs &a, int32_t v)
 {
     return __ldg(a.Yc + v);
+}
+
+// Label of a rarely referenced rank: read from L2 without taking an L1 line
+// (such gathers almost never hit L1, and the lines they would take are what
+// keeps the other loads in flight).
+__device__ __forceinline__ uint32_t cold_label_of(const PullArgs &a, int32_t v)
+{
+    uint32_t r;
+    asm("ld.global.cg.u8 %0, [%1];" : "=r"(r) : "l"(a.Yc + v));
+    return r;
 }
 
 // column of local cell j (the tile's first cell is a multiple of cols);
@@ -706,11 +724,13 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
         }
     };
     // the labels of the hot_n most referenced ranks come from the CTA's
-    // shared-memory copy, the rest through L1
+    // shared-memory copy, those below cold_from through L1, the rest from L2
     auto fetch = [&](int32_t v) -> uint32_t {
         if (MULTI)
             return (uint32_t)v;
-        return v < hot_n ? (uint32_t)hot[v] : label_of(a, v);
+        if (v < hot_n)
+            return (uint32_t)hot[v];
+        return v < a.cold_from ? label_of(a, v) : cold_label_of(a, v);
     };
     const int head =
         min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
@@ -1251,6 +1271,7 @@ static PullArgs pull_args(const Csr &g, int32_t L, int32_t classes,
                           const DevStatus *st)
 {
     PullArgs a = {};
+    a.cold_from = INT32_MAX;
     a.rowptr = g.rowptr;
     a.col = g.col;
     a.val = laplacian ? g.lap_val : g.val;
@@ -1306,6 +1327,7 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess)
         return e;
+    a.cold_from = kLightColdFrom;
     const int threads = kGroups * kGroupThreads;
     const bool w = weighted || laplacian;
     if (L > 1)
@@ -1339,6 +1361,7 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     a.group_bytes =
         (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);
     a.hot_n = L > 1 ? 0 : (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
+    a.cold_from = a.hot_n;
     const size_t area = (size_t)(kHeavyThreads / 32) * a.group_bytes;
     const size_t smem = plan_shared(area + (size_t)a.hot_n, a);
     a.hot_off = a.area_off + (int32_t)area;
