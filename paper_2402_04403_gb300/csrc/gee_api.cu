@@ -294,6 +294,9 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
     if (host_z && g.chunks > 0) {
         const int sms = sm_count();
         const int light_ctas = sms / 4 > 0 ? sms / 4 : 1;
+        // light rows on a quarter of the SMs; hub chunks, then every hub
+        // row, on the rest -- the two sides write disjoint cells of Z, so
+        // the hub rows cross the host link while the light rows do
         SideStream side(stream);
         GEE_CHECK_CUDA(side.fork());
         {
@@ -304,18 +307,19 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                                              sms - light_ctas));
         }
         {
+            ProfScope p("k_hub_fixup", side.stream());
+            GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
+                                            counts, Z, hub_part, true, st,
+                                            side.stream()));
+        }
+        {
             ProfScope p("k_pull_light", stream);
             GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
                                              tile_row, ntiles, Yc, counts, Z,
-                                             work, st, stream, light_ctas));
+                                             work, st, stream, light_ctas,
+                                             true));
         }
         GEE_CHECK_CUDA(side.join());
-        if (g.hubs > 0) {
-            ProfScope p("k_hub_fixup", stream);
-            GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
-                                            counts, Z, hub_part, true, st,
-                                            stream));
-        }
         return GEE_OK;
     }
     {
@@ -853,7 +857,8 @@ gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
             b += (c.nnz_main + c.hub_arcs + 8) * 4;
         if (c.lap_val)
             b += (c.nnz_main + c.hub_arcs + 8) * 4;
-        b += c.hubs * 16 + c.chunks * 12 + (c.n + 1) * 4;
+        b += c.hubs * 16 + c.chunks * 12 + (c.n + 1) * 4 +
+             ((c.n + 31) / 32 + 1) * 4;
         *device_bytes = b;
     }
     return GEE_OK;

@@ -230,6 +230,22 @@ __global__ void k_hub_list(const uint32_t *__restrict__ deg,
     }
 }
 
+// bits[w] bit b = hub[32w + b]: one warp ballot per word.
+__global__ void k_hub_bits(const uint32_t *__restrict__ hub, int64_t n,
+                           uint32_t *__restrict__ bits)
+{
+    const int64_t words = (n + 31) >> 5;
+    const int64_t lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < words; w += nwarps) {
+        const int64_t i = (w << 5) + lane;
+        const uint32_t b = __ballot_sync(0xffffffffu, i < n && hub[i] != 0u);
+        if (lane == 0)
+            bits[w] = b;
+    }
+}
+
 __global__ void k_chunk_list(const int64_t *__restrict__ hub_ptr,
                              const int32_t *__restrict__ hub_chunk0,
                              int64_t hubs, int32_t *__restrict__ chunk_hub,
@@ -566,6 +582,8 @@ struct PullArgs {
     int32_t hot_off, hot_n;  // heavy kernel: shared copy of the labels of
                              // ranks [0, hot_n), a multiple of 16
     int32_t cold_from;       // labels of ranks >= cold_from are read past L1
+    const uint32_t *hub_bits;  // light kernel: if set, hub rows' cells are
+                               // left untouched (bit r: row r is a hub row)
     int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
                              // k_pull_heavy; 0: every chunk leaves partials
                              // and k_hub_fixup writes all hub rows
@@ -797,6 +815,13 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
 // Row starts of a tile, loaded ahead into registers: entry i = gt + j*128
 // of rowptr[r0 .. r1] for the thread with group rank gt.
 constexpr int kRowsAhead = 3;  // (4,096 / 16 + 1) row starts over 128 threads
+// Floats in a 128-byte line, and the float offset of p within its line.
+constexpr int kLineFloats = 32;
+__device__ __forceinline__ int line_offset(const float *p)
+{
+    return (int)((reinterpret_cast<uintptr_t>(p) >> 2) & (kLineFloats - 1));
+}
+
 struct TileRows {
     int32_t r0 = 0, r1 = 0;
     int64_t A0 = 0;
@@ -833,8 +858,8 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
     const int64_t g0 = (int64_t)tr.r0 * K;  // first Z cell of the tile
     // acc[off + j] holds cell g0 + j, off = the cell's float offset within
-    // its 16-byte block of Z (any 4-byte aligned Z)
-    const int off = (int)((reinterpret_cast<uintptr_t>(a.Z + g0) >> 2) & 3);
+    // its 128-byte line of Z (any 4-byte aligned Z)
+    const int off = line_offset(a.Z + g0);
     const int cells = NR * K;
     const int NA = NR > 0 ? rp[NR] : 0;
 
@@ -843,22 +868,22 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
         TileCells tc{rp, NR, K, off, 0, 0};
         sweep_arcs<WEIGHTED, MULTI, kGroupThreads>(
             a, a.col + tr.A0, WEIGHTED ? a.val + tr.A0 : nullptr, NA, gt, acc,
-            a.max_rows * K + 8 + (gt & 31), tc);
+            a.max_rows * K + kLineFloats + 4 + (gt & 31), tc);
     }
     group_sync(g);
     before_write();
 
     // the tile's rows are contiguous in Z: scale once and stream out with
-    // 16-byte stores between an unaligned head and tail; all-zero quads
-    // (most of them: isolated nodes, sparse rows) skip the conversion
+    // 16-byte stores between an unaligned head and tail; the head runs to a
+    // 128-byte line, so each warp's stores cover whole lines (which is what
+    // a page-locked host Z written over the host link needs for its full
+    // rate); all-zero quads (most of them: isolated nodes, sparse rows) skip
+    // the conversion
     float *z = a.Z + g0;
-    const int head = min((4 - off) & 3, cells);
-    if (gt < head)
-        __stcs(z + gt, cell_value<WEIGHTED>(acc[off + gt], class_of(a, gt), nk,
-                                            table));
+    const int head = min((kLineFloats - off) & (kLineFloats - 1), cells);
     const int nq = (cells - head) >> 2;
-    for (int q = gt; q < nq; q += kGroupThreads) {
-        const int j0 = head + 4 * q;
+    const int tail0 = head + 4 * nq;
+    auto quad_values = [&](int j0) {
         const uint4 c4 = *reinterpret_cast<const uint4 *>(acc + off + j0);
         float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
@@ -873,14 +898,50 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
             }
             o4 = make_float4(o[0], o[1], o[2], o[3]);
         }
-        __stcs(reinterpret_cast<float4 *>(z + j0), o4);
+        return o4;
+    };
+    auto scalar_value = [&](int j) {
+        return cell_value<WEIGHTED>(acc[off + j], class_of(a, j), nk, table);
+    };
+    if (a.hub_bits == nullptr) {
+        if (gt < head)
+            __stcs(z + gt, scalar_value(gt));
+        for (int q = gt; q < nq; q += kGroupThreads) {
+            const int j0 = head + 4 * q;
+            __stcs(reinterpret_cast<float4 *>(z + j0), quad_values(j0));
+        }
+        if (gt < cells - tail0)
+            __stcs(z + tail0 + gt, scalar_value(tail0 + gt));
+        return;
     }
-    const int tail0 = head + 4 * nq;
-    if (gt < cells - tail0) {
-        const int j = tail0 + gt;
-        __stcs(z + j, cell_value<WEIGHTED>(acc[off + j], class_of(a, j), nk,
-                                           table));
+    // hub rows' cells are left to k_hub_fixup: a quad that touches one is
+    // written cell by cell
+    auto hub_cell = [&](int j) {
+        const int64_t r = tr.r0 + (a.cols == 1 ? j : (int)__umulhi((unsigned)j, a.kmagic));
+        return ((__ldg(a.hub_bits + (r >> 5)) >> (r & 31)) & 1u) != 0u;
+    };
+    if (gt < head && !hub_cell(gt))
+        __stcs(z + gt, scalar_value(gt));
+    for (int q = gt; q < nq; q += kGroupThreads) {
+        const int j0 = head + 4 * q;
+        const float4 o4 = quad_values(j0);
+        const bool h0 = hub_cell(j0), h1 = hub_cell(j0 + 1),
+                   h2 = hub_cell(j0 + 2), h3 = hub_cell(j0 + 3);
+        if (!(h0 | h1 | h2 | h3)) {
+            __stcs(reinterpret_cast<float4 *>(z + j0), o4);
+        } else {
+            if (!h0)
+                __stcs(z + j0, o4.x);
+            if (!h1)
+                __stcs(z + j0 + 1, o4.y);
+            if (!h2)
+                __stcs(z + j0 + 2, o4.z);
+            if (!h3)
+                __stcs(z + j0 + 3, o4.w);
+        }
     }
+    if (gt < cells - tail0 && !hub_cell(tail0 + gt))
+        __stcs(z + tail0 + gt, scalar_value(tail0 + gt));
 }
 
 // Each group pipelines its tiles: it draws tile t+1 before the setup
@@ -924,8 +985,7 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
         // setup: zero the accumulators, publish the row starts
         const int NR = cur.r1 - cur.r0;
         const int cells = NR * K;
-        const int off = (int)((reinterpret_cast<uintptr_t>(
-                                   a.Z + (int64_t)cur.r0 * K) >> 2) & 3);
+        const int off = line_offset(a.Z + (int64_t)cur.r0 * K);
         {
             uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
             for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
@@ -1157,6 +1217,13 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
     GEE_TRY(al.alloc((void **)&base, sizeof(int64_t) * (n + 1)));
     GEE_TRY(al.alloc((void **)&cursor, sizeof(uint32_t) * (n + 1)));
     GEE_TRY(persist.alloc((void **)&g.hub_ptr, sizeof(int64_t) * (g.hubs + 1)));
+    GEE_TRY(persist.alloc((void **)&g.hub_bits,
+                          sizeof(uint32_t) * ((n + 31) / 32 + 1)));
+    GEE_TRY(cudaMemsetAsync(g.hub_bits, 0,
+                            sizeof(uint32_t) * ((n + 31) / 32 + 1), stream));
+    if (n > 0)
+        k_hub_bits<<<grid_for((n + 31) / 32 * 32, 256, sms * 8), 256, 0,
+                     stream>>>(hub, n, g.hub_bits);
     if (g.hubs > 0) {
         uint32_t *hub_deg, *hub_nchunks;
         GEE_TRY(persist.alloc((void **)&g.hub_row, sizeof(int32_t) * g.hubs));
@@ -1307,19 +1374,22 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas)
+                              cudaStream_t stream, int ctas, bool skip_hub_rows)
 {
     if (ntiles == 0)
         return cudaSuccess;
     PullArgs a = pull_args(g, L, classes, laplacian, tile_row, ntiles, Yc,
                            counts, Z, nullptr, work, st);
+    a.hub_bits = skip_hub_rows ? g.hub_bits : nullptr;
     const int K = a.cols;
     const int C = row_cost(K);
     a.max_rows = (kTileUnits + C - 1) / C;
     const size_t rpb = align16((size_t)(a.max_rows + 2) * 4);
-    // +8 cells: the offset (< 4) and the 16-byte rounding of the zeroing;
-    // then 32 sink cells (one per lane) for arcs of unknown label
-    const size_t accb = align16((size_t)(a.max_rows * K + 8 + 32) * 4);
+    // + kLineFloats + 4 cells: the offset (< kLineFloats) and the 16-byte
+    // rounding of the zeroing; then 32 sink cells (one per lane) for arcs of
+    // unknown label
+    const size_t accb =
+        align16((size_t)(a.max_rows * K + kLineFloats + 4 + 32) * 4);
     a.acc_off = (int32_t)rpb;
     a.slot_off = (int32_t)(rpb + accb);
     a.group_bytes = (int32_t)(a.slot_off + 16);

@@ -176,6 +176,7 @@ struct Csr {
     int32_t *col = nullptr;         // [nnz_main + pad] target ranks
     float *val = nullptr;           // [nnz_main + pad] or null
     int32_t *hub_row = nullptr;     // [hubs]
+    uint32_t *hub_bits = nullptr;   // [n/32 + 1] bit i of word i/32: row i is a hub row
     int64_t *hub_ptr = nullptr;     // [hubs+1] into col_h
     int32_t *col_h = nullptr;       // [hub_arcs + pad]
     float *val_h = nullptr;
@@ -265,14 +266,17 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 // ctas: persistent CTAs (0 = one per SM).  partials_only: k_pull_heavy
 // leaves every chunk's sums in hub_part (never writing Z) and
 // launch_hub_fixup(all_rows = true) writes every hub row -- so the two
-// pull kernels may run at the same time on disjoint SMs.
+// pull kernels may run at the same time on disjoint SMs.  skip_hub_rows:
+// k_pull_light leaves the cells of hub rows untouched (instead of zeroing
+// them), so launch_hub_fixup(all_rows = true) may run at the same time too.
 cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian,
                               const int32_t *tile_row,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas = 0);
+                              cudaStream_t stream, int ctas = 0,
+                              bool skip_hub_rows = false);
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,

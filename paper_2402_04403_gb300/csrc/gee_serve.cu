@@ -619,7 +619,8 @@ gee_status gee_server_add_graph(gee_server *srv, const int32_t *edges_h,
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
     // resident CSR: row pointers, ranks, arcs (+ values) and hub tables
-    const int64_t est = align256((n + 1) * 12) + align256(2 * s * 4 + 64) +
+    const int64_t est = align256((n + 1) * 12) + align256((n + 31) / 32 * 4 + 4) +
+                        align256(2 * s * 4 + 64) +
                         (weights_h != nullptr ? align256(2 * s * 4 + 64) : 0) +
                         align256(2 * s / kHubDegree * 24 + 64) + kSlack;
     {

@@ -337,3 +337,33 @@ def test_multi_label_limits(gee, tiny_sbm_graph):
         with pytest.raises(gee.GeeError) as ei:
             g.embed_multi(_dev(Ys), 5)
         assert ei.value.name == "GEE_ERR_LABEL_RANGE"
+
+
+@pytest.mark.parametrize("K", [1, 3, 9, 50])
+@pytest.mark.parametrize("variant", ["unit", "weighted", "laplacian"])
+def test_graph_host_direct_write_hub_rows_and_offsets(gee, rmat16, K, variant):
+    """The direct-write form of gee_embed_graph_host writes light rows from
+    one kernel and hub rows from another at the same time: every cell of a
+    page-locked Z (placed at a float offset that leaves every line
+    alignment) gets its value, and no float around it changes.  Unit
+    weights: the oracle bit for bit; float weights (shared-memory float
+    atomics, so the summation order varies between calls): the oracle
+    within 1e-5."""
+    import torch
+    edges, n = rmat16
+    w = graphgen.weights(edges.shape[0], seed=43) if variant != "unit" else None
+    lap = variant == "laplacian"
+    Y = graphgen.labels(n, K, seed=44 + K, frac_unlabeled=0.2)
+    for shift in (0, 5):
+        buf = torch.full((n * K + 64,), float("nan"), dtype=torch.float32).pin_memory()
+        Zp = buf[shift:shift + n * K].view(n, K)
+        with gee.Graph(_dev(edges), n, weights=None if w is None else _dev(w)) as g:
+            g.embed_host(torch.from_numpy(Y).pin_memory(), K, laplacian=lap, out=Zp)
+        got = Zp.numpy()
+        if w is None:
+            assert np.array_equal(got, oracle.embed_counts32(edges, Y, K)), shift
+        else:
+            assert_weighted_close(got, oracle.embed(edges, Y, K, weights=w, laplacian=lap),
+                                  f"host {variant} K={K} shift={shift}")
+        rest = torch.cat([buf[:shift], buf[shift + n * K:]])
+        assert torch.all(torch.isnan(rest)), shift
