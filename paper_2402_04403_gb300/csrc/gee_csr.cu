@@ -883,10 +883,14 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     const int head = min((kLineFloats - off) & (kLineFloats - 1), cells);
     const int nq = (cells - head) >> 2;
     const int tail0 = head + 4 * nq;
+    // each cell read here is cleared again, so the accumulators are zero
+    // for the group's next tile
     auto quad_values = [&](int j0) {
-        const uint4 c4 = *reinterpret_cast<const uint4 *>(acc + off + j0);
+        uint4 *p4 = reinterpret_cast<uint4 *>(acc + off + j0);
+        const uint4 c4 = *p4;
         float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
+            *p4 = make_uint4(0u, 0u, 0u, 0u);
             int k = class_of(a, j0);
             const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
             float o[4];
@@ -901,7 +905,9 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
         return o4;
     };
     auto scalar_value = [&](int j) {
-        return cell_value<WEIGHTED>(acc[off + j], class_of(a, j), nk, table);
+        const uint32_t c = acc[off + j];
+        acc[off + j] = 0u;
+        return cell_value<WEIGHTED>(c, class_of(a, j), nk, table);
     };
     if (a.hub_bits == nullptr) {
         if (gt < head)
@@ -920,8 +926,11 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
         const int64_t r = tr.r0 + (a.cols == 1 ? j : (int)__umulhi((unsigned)j, a.kmagic));
         return ((__ldg(a.hub_bits + (r >> 5)) >> (r & 31)) & 1u) != 0u;
     };
-    if (gt < head && !hub_cell(gt))
-        __stcs(z + gt, scalar_value(gt));
+    if (gt < head) {
+        const float v = scalar_value(gt);
+        if (!hub_cell(gt))
+            __stcs(z + gt, v);
+    }
     for (int q = gt; q < nq; q += kGroupThreads) {
         const int j0 = head + 4 * q;
         const float4 o4 = quad_values(j0);
@@ -940,15 +949,22 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                 __stcs(z + j0 + 3, o4.w);
         }
     }
-    if (gt < cells - tail0 && !hub_cell(tail0 + gt))
-        __stcs(z + tail0 + gt, scalar_value(tail0 + gt));
+    if (gt < cells - tail0) {
+        const float v = scalar_value(tail0 + gt);
+        if (!hub_cell(tail0 + gt))
+            __stcs(z + tail0 + gt, v);
+    }
 }
 
 // Each group pipelines its tiles: it draws tile t+1 before the setup
 // barrier of tile t, loads t+1's row range while sweeping t and t+1's row
 // starts while writing t, so a tile's setup finds its row starts in
-// registers.  Three group barriers per tile: setup published, accumulators
-// complete, accumulators free again.
+// registers.  The accumulators are zeroed once; the write phase clears
+// every cell it reads, so a tile starts on zeros.  Two group barriers per
+// tile: setup published (which also orders the previous tile's writes and
+// clears before this tile's sweep), accumulators complete.  The setup
+// rewrites only the row starts, which no thread reads after the second
+// barrier.
 template <bool WEIGHTED, bool MULTI>
 __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     k_pull_light(PullArgs a)
@@ -967,6 +983,13 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     int32_t *rp = reinterpret_cast<int32_t *>(gs);
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
     const int32_t K = a.cols;
+    {
+        // every cell a tile can use: max_rows rows at a line offset
+        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+        const int quads = (a.max_rows * K + kLineFloats + 3) / 4;
+        for (int c = gt; c < quads; c += kGroupThreads)
+            acc4[c] = make_uint4(0u, 0u, 0u, 0u);
+    }
 
     if (gt == 0)
         slot[0] = (long long)atomicAdd(a.work, 1ull);
@@ -982,15 +1005,8 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
         // the next tile, read by the group after the setup barrier below
         if (gt == 0)
             slot[(it + 1) & 1] = (long long)atomicAdd(a.work, 1ull);
-        // setup: zero the accumulators, publish the row starts
+        // setup: publish the row starts (the accumulators are zero)
         const int NR = cur.r1 - cur.r0;
-        const int cells = NR * K;
-        const int off = line_offset(a.Z + (int64_t)cur.r0 * K);
-        {
-            uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-            for (int c = gt; c < (cells + off + 3) / 4; c += kGroupThreads)
-                acc4[c] = make_uint4(0u, 0u, 0u, 0u);
-        }
 #pragma unroll
         for (int j = 0; j < kRowsAhead; ++j) {
             const int i = gt + j * kGroupThreads;
@@ -1008,7 +1024,6 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
             if (next < a.ntiles)  // in flight during the write phase
                 load_tile_rows(a, gt, nxt);
         });
-        group_sync(g);
         item = next;
         cur = nxt;
     }
