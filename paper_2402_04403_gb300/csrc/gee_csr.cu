@@ -544,7 +544,7 @@ constexpr int kGroups = 8;
 constexpr int kUnroll = 8;        // arcs in flight per thread
 constexpr int kTableCounts = 8;   // counts below this convert by table
 constexpr int kHeavyThreads = 1024;
-constexpr int kHeavyCopies = 1;   // per-warp accumulator copies
+constexpr int kHeavyCopyCells = 128;  // float sums: copies x cols up to this
 constexpr int kChunkGrab = 4;     // hub chunks a warp draws at a time
 constexpr int kHotLabels = 131072; // hub-row kernel: labels kept in shared memory
 constexpr int kLightColdFrom = 1 << 18;  // row-tile kernel: ranks read past L1
@@ -582,6 +582,7 @@ struct PullArgs {
     int32_t hot_off, hot_n;  // heavy kernel: shared copy of the labels of
                              // ranks [0, hot_n), a multiple of 16
     int32_t cold_from;       // labels of ranks >= cold_from are read past L1
+    int32_t copies;          // heavy kernel: accumulator copies per warp
     const uint32_t *hub_bits;  // light kernel: if set, hub rows' cells are
                                // left untouched (bit r: row r is a hub row)
     int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
@@ -1051,7 +1052,8 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     uint32_t *acc = reinterpret_cast<uint32_t *>(sm + a.area_off +
                                                  (size_t)wib * a.group_bytes);
     float *accf = reinterpret_cast<float *>(acc);
-    const int copy = (lane & (kHeavyCopies - 1)) * K;
+    const int copies = WEIGHTED ? a.copies : 1;  // a power of two
+    const int copy = (lane & (copies - 1)) * K;
     // warps draw kChunkGrab consecutive chunks at a time from a counter
     for (;;) {
         unsigned long long g0 = 0;
@@ -1063,7 +1065,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         const int64_t c_lo = (int64_t)g0;
         const int64_t c_hi = min(c_lo + kChunkGrab, a.chunks);
     for (int64_t c = c_lo; c < c_hi; ++c) {
-        for (int i = lane; i < kHeavyCopies * K; i += 32)
+        for (int i = lane; i < copies * K; i += 32)
             acc[i] = 0u;
         __syncwarp();
         const int32_t h = a.chunk_hub[c];
@@ -1073,7 +1075,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         ChunkCells cells{copy};
         sweep_arcs<WEIGHTED, MULTI, 32>(a, a.col_h + b,
                                  WEIGHTED ? a.val_h + b : nullptr, n, lane,
-                                 acc, kHeavyCopies * K + lane, cells, hot, hot_n);
+                                 acc, copies * K + lane, cells, hot, hot_n);
         __syncwarp();
         const bool whole =
             a.hub_direct && a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
@@ -1082,14 +1084,12 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
             uint32_t bits;
             if (WEIGHTED) {
                 float s = 0.0f;
-#pragma unroll
-                for (int r = 0; r < kHeavyCopies; ++r)
+                for (int r = 0; r < copies; ++r)
                     s += accf[r * K + k];
                 bits = __float_as_uint(s);
             } else {
                 uint32_t s = 0;
-#pragma unroll
-                for (int r = 0; r < kHeavyCopies; ++r)
+                for (int r = 0; r < copies; ++r)
                     s += acc[r * K + k];
                 bits = s;
             }
@@ -1441,16 +1441,22 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     cudaError_t e0 = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e0 != cudaSuccess)
         return e0;
-    // kHeavyCopies accumulators of cols cells, then 32 sink cells, then the
-    // hot labels (at most the first n ranks, a multiple of 16 bytes)
-    a.group_bytes =
-        (int32_t)align16((size_t)(kHeavyCopies * a.cols + 32) * 4);
+    // `copies` accumulators of cols cells per warp, then 32 sink cells, then
+    // the hot labels (at most the first n ranks, a multiple of 16 bytes).
+    // Integer counts use one copy; float sums spread the lanes over up to
+    // four (lane l adds into copy l mod copies): shared-memory float adds
+    // from several lanes to one cell serialise, and a few classes take all
+    // of a warp's adds
+    const bool w = weighted || laplacian;
+    a.copies = 1;
+    while (w && a.copies < 4 && 2 * a.copies * a.cols <= kHeavyCopyCells)
+        a.copies *= 2;
+    a.group_bytes = (int32_t)align16((size_t)(a.copies * a.cols + 32) * 4);
     a.hot_n = L > 1 ? 0 : (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
     a.cold_from = a.hot_n;
     const size_t area = (size_t)(kHeavyThreads / 32) * a.group_bytes;
     const size_t smem = plan_shared(area + (size_t)a.hot_n, a);
     a.hot_off = a.area_off + (int32_t)area;
-    const bool w = weighted || laplacian;
     if (L > 1)
         return w ? launch_persistent(k_pull_heavy<true, true>, kHeavyThreads,
                                      smem, a, stream, ctas)
