@@ -13,6 +13,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int g_sms[kMaxDevices];
+int g_smem[kMaxDevices];
 cudaMemPool_t g_pool[kMaxDevices];
 bool g_pool_ready[kMaxDevices];
 
@@ -278,7 +279,7 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         }
         return GEE_OK;
     }
-    const int64_t ntiles = pull_tiles(g, cols);
+    const int64_t ntiles = pull_tiles(g, cols, host_z);
     int32_t *tile_row = nullptr;
     void *hub_part = nullptr;
     unsigned long long *work = nullptr;
@@ -289,7 +290,8 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
     {
         ProfScope p("k_partition", stream);
-        GEE_CHECK_CUDA(launch_partition(g, cols, tile_row, ntiles, stream));
+        GEE_CHECK_CUDA(
+            launch_partition(g, cols, tile_row, ntiles, host_z, stream));
     }
     if (host_z && g.chunks > 0) {
         const int sms = sm_count();
@@ -326,7 +328,7 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         ProfScope p("k_pull_light", stream);
         GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
                                          tile_row, ntiles, Yc, counts, Z,
-                                         work, st, stream));
+                                         work, st, stream, 0, host_z));
     }
     if (g.chunks > 0) {
         ProfScope p("k_pull_heavy", stream);
@@ -448,6 +450,23 @@ int sm_count()
         g_sms[dev] = sms;
     }
     return g_sms[dev];
+}
+
+int max_block_smem()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return 48 << 10;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_smem[dev] == 0) {
+        int b = 0;
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                   dev) != cudaSuccess ||
+            b <= 0)
+            b = 48 << 10;
+        g_smem[dev] = b;
+    }
+    return g_smem[dev];
 }
 
 }  // namespace gee

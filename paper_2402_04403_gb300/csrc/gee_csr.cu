@@ -7,7 +7,7 @@
 //   build_csr      edge list -> symmetric CSR (each edge (u,v,w) gives arcs
 //                  u->v and v->u), rows with more than kHubDegree arcs moved
 //                  to a separate hub CSR cut into chunks of kHubChunk arcs.
-//   k_partition    splits rows + arcs into tiles of kTileUnits merged units
+//   k_partition    splits rows + arcs into tiles of 1,024 (or 4,096) merged units
 //                  (1 per arc, max(K,16) per row) so every tile moves about
 //                  the same number of bytes.
 //   k_pull_light   row tiles of the rows with at most kHubDegree arcs:
@@ -483,13 +483,13 @@ __global__ void k_lap_values_hub(const int32_t *__restrict__ hub_row,
 // Units: 1 per arc, C = max(K, 16) per row (its Z write; the floor keeps the
 // rows of one tile, and so the shared-memory row table, bounded for small K).
 // tile_row[t] = first row whose end unit E_r = rowptr[r+1] + r*C lies at or
-// after t*kTileUnits (n if none).  Tile t owns rows [tile_row[t],
-// tile_row[t+1]) with all their arcs: at most ceil(kTileUnits / C) rows and
-// kTileUnits + kHubDegree arcs.
+// after t*units (n if none).  Tile t owns rows [tile_row[t],
+// tile_row[t+1]) with all their arcs: at most ceil(units / C) rows and
+// units + kHubDegree arcs.
 __device__ __host__ inline int row_cost(int32_t K) { return K > 16 ? K : 16; }
 
 __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
-                            int32_t K, int64_t ntiles,
+                            int32_t K, int64_t ntiles, int32_t units,
                             int32_t *__restrict__ tile_row)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -500,7 +500,7 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
         return;
     }
     const int64_t C = row_cost(K);
-    const int64_t diag = t * kTileUnits;
+    const int64_t diag = t * units;
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -526,12 +526,16 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 // (hub rows 6.97 -> 6.41 ms, row tiles 5.47 -> 5.34 ms on the paper-scale
 // graph).
 //
-// k_pull_light: rows with at most kHubDegree arcs.  NG independent groups of
-//   128 threads (own named barrier each) take row tiles from a global
-//   counter; per tile: zero the accumulators and load the row starts, sweep
-//   the arcs (16-byte loads, label, binary search for the row, shared
-//   atomic per (row, class)), write the tile's Z rows -- contiguous in Z --
-//   once with 16-byte stores.
+// k_pull_light: rows with at most kHubDegree arcs.  Every warp of the CTA
+//   is an independent group that takes row tiles of kTileUnits units from a
+//   global counter; per tile: load the row starts, sweep the arcs (16-byte
+//   loads, label, binary search for the row, shared atomic per (row,
+//   class)), write the tile's Z rows -- contiguous in Z -- once with
+//   16-byte stores.  One warp per tile needs only warp barriers, so no warp
+//   waits for the slowest of several (groups of 4 warps on 4,096-unit
+//   tiles: 5.22 ms on the paper-scale graph, one warp on 1,024 units:
+//   4.89 ms).  The launch takes as many warps as the tiles' accumulators
+//   fit in shared memory, at most 32.
 //   Rows kept in the hub CSR have no arcs here and get zeros.
 // k_pull_heavy: rows with more than kHubDegree arcs, cut into chunks of at
 //   most kHubChunk arcs.  One warp per chunk, no block barriers; warps draw
@@ -539,8 +543,16 @@ __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t n,
 //   than fixed ranges of equal arc counts: no tail of idle warps).  A single-chunk row's Z row
 //   is written directly, overwriting the zeros of k_pull_light (which runs
 //   first); longer rows leave per-chunk partial sums for k_hub_fixup.
-constexpr int kGroupThreads = 128;
-constexpr int kGroups = 8;
+// Row-tile shapes: groups of GT threads on tiles of 32*GT units.  GT = 32
+// (one warp per tile, warp barriers) for Z in device memory; GT = 128
+// (named barriers) for page-locked host Z, whose larger tiles leave fewer
+// partial 128-byte lines at tile ends for the host link.
+constexpr int kDeviceGroup = 32;
+constexpr int kHostGroup = 128;
+template <int GT>
+constexpr int tile_units() { return 32 * GT; }
+static_assert(tile_units<kDeviceGroup>() == kTileUnits,
+              "scratch for tile starts is sized by kTileUnits");
 constexpr int kUnroll = 8;        // arcs in flight per thread
 constexpr int kTableCounts = 8;   // counts below this convert by table
 constexpr int kHeavyThreads = 1024;
@@ -590,9 +602,13 @@ struct PullArgs {
                              // and k_hub_fixup writes all hub rows
 };
 
+template <int GT>
 __device__ __forceinline__ void group_sync(int g)
 {
-    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory");
+    if constexpr (GT == 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GT) : "memory");
 }
 
 // Label of rank v (read-only path; the most referenced labels -- the front
@@ -813,9 +829,12 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
     }
 }
 
-// Row starts of a tile, loaded ahead into registers: entry i = gt + j*128
+// Row starts of a tile, loaded ahead into registers: entry i = gt + j*32
 // of rowptr[r0 .. r1] for the thread with group rank gt.
-constexpr int kRowsAhead = 3;  // (4,096 / 16 + 1) row starts over 128 threads
+constexpr int kRowsAhead = 3;
+static_assert(kRowsAhead * kDeviceGroup >= tile_units<kDeviceGroup>() / 16 + 1 &&
+                  kRowsAhead * kHostGroup >= tile_units<kHostGroup>() / 16 + 1,
+              "a tile's row starts fit in kRowsAhead per thread");
 // Floats in a 128-byte line, and the float offset of p within its line.
 constexpr int kLineFloats = 32;
 __device__ __forceinline__ int line_offset(const float *p)
@@ -829,6 +848,7 @@ struct TileRows {
     int64_t rv[kRowsAhead];
 };
 
+template <int GT>
 __device__ __forceinline__ void load_tile_rows(const PullArgs &a, int gt,
                                                TileRows &tr)
 {
@@ -836,7 +856,7 @@ __device__ __forceinline__ void load_tile_rows(const PullArgs &a, int gt,
     const int NR = tr.r1 - tr.r0;
 #pragma unroll
     for (int j = 0; j < kRowsAhead; ++j) {
-        const int i = gt + j * kGroupThreads;
+        const int i = gt + j * GT;
         tr.rv[j] = i <= NR ? a.rowptr[tr.r0 + i] : 0;
     }
 }
@@ -845,7 +865,7 @@ __device__ __forceinline__ void load_tile_rows(const PullArgs &a, int gt,
 // barrier): sweep its arcs into the accumulators, barrier, then scale and
 // write its Z rows.  `before_write` runs between the barrier and the write
 // phase (the caller issues the next tile's loads there).
-template <bool WEIGHTED, bool MULTI, class BeforeWrite>
+template <bool WEIGHTED, bool MULTI, int GT, class BeforeWrite>
 __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                                          unsigned char *gs,
                                          const uint32_t *nk,
@@ -867,11 +887,11 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     // sweep: the row of arc i is the last row starting at or before i
     if (NA > 0) {
         TileCells tc{rp, NR, K, off, 0, 0};
-        sweep_arcs<WEIGHTED, MULTI, kGroupThreads>(
+        sweep_arcs<WEIGHTED, MULTI, GT>(
             a, a.col + tr.A0, WEIGHTED ? a.val + tr.A0 : nullptr, NA, gt, acc,
             a.max_rows * K + kLineFloats + 4 + (gt & 31), tc);
     }
-    group_sync(g);
+    group_sync<GT>(g);
     before_write();
 
     // the tile's rows are contiguous in Z: scale once and stream out with
@@ -913,7 +933,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     if (a.hub_bits == nullptr) {
         if (gt < head)
             __stcs(z + gt, scalar_value(gt));
-        for (int q = gt; q < nq; q += kGroupThreads) {
+        for (int q = gt; q < nq; q += GT) {
             const int j0 = head + 4 * q;
             __stcs(reinterpret_cast<float4 *>(z + j0), quad_values(j0));
         }
@@ -932,7 +952,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
         if (!hub_cell(gt))
             __stcs(z + gt, v);
     }
-    for (int q = gt; q < nq; q += kGroupThreads) {
+    for (int q = gt; q < nq; q += GT) {
         const int j0 = head + 4 * q;
         const float4 o4 = quad_values(j0);
         const bool h0 = hub_cell(j0), h1 = hub_cell(j0 + 1),
@@ -966,8 +986,8 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
 // clears before this tile's sweep), accumulators complete.  The setup
 // rewrites only the row starts, which no thread reads after the second
 // barrier.
-template <bool WEIGHTED, bool MULTI>
-__global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
+template <bool WEIGHTED, bool MULTI, int GT>
+__global__ void __launch_bounds__(1024, 1)
     k_pull_light(PullArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -977,8 +997,8 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
     float *table = reinterpret_cast<float *>(sm + ((a.cols * 4 + 15) & ~15));
     load_shared<WEIGHTED>(a, nk, table);
     __syncthreads();
-    const int g = threadIdx.x / kGroupThreads;
-    const int gt = threadIdx.x - g * kGroupThreads;
+    const int g = threadIdx.x / GT;
+    const int gt = threadIdx.x - g * GT;
     unsigned char *gs = sm + a.area_off + (size_t)g * a.group_bytes;
     long long *slot = reinterpret_cast<long long *>(gs + a.slot_off);
     int32_t *rp = reinterpret_cast<int32_t *>(gs);
@@ -988,19 +1008,19 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
         // every cell a tile can use: max_rows rows at a line offset
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
         const int quads = (a.max_rows * K + kLineFloats + 3) / 4;
-        for (int c = gt; c < quads; c += kGroupThreads)
+        for (int c = gt; c < quads; c += GT)
             acc4[c] = make_uint4(0u, 0u, 0u, 0u);
     }
 
     if (gt == 0)
         slot[0] = (long long)atomicAdd(a.work, 1ull);
-    group_sync(g);
+    group_sync<GT>(g);
     int64_t item = slot[0];
     TileRows cur;
     if (item < a.ntiles) {
         cur.r0 = a.tile_row[item];
         cur.r1 = a.tile_row[item + 1];
-        load_tile_rows(a, gt, cur);
+        load_tile_rows<GT>(a, gt, cur);
     }
     for (int it = 0; item < a.ntiles; ++it) {
         // the next tile, read by the group after the setup barrier below
@@ -1010,20 +1030,20 @@ __global__ void __launch_bounds__(kGroups *kGroupThreads, 1)
         const int NR = cur.r1 - cur.r0;
 #pragma unroll
         for (int j = 0; j < kRowsAhead; ++j) {
-            const int i = gt + j * kGroupThreads;
+            const int i = gt + j * GT;
             if (i <= NR)
                 rp[i] = (int32_t)(cur.rv[j] - cur.A0);
         }
-        group_sync(g);
+        group_sync<GT>(g);
         const int64_t next = slot[(it + 1) & 1];
         TileRows nxt;
         if (next < a.ntiles) {  // in flight during the sweep
             nxt.r0 = a.tile_row[next];
             nxt.r1 = a.tile_row[next + 1];
         }
-        row_tile<WEIGHTED, MULTI>(a, g, gt, gs, nk, table, cur, [&]() {
+        row_tile<WEIGHTED, MULTI, GT>(a, g, gt, gs, nk, table, cur, [&]() {
             if (next < a.ntiles)  // in flight during the write phase
-                load_tile_rows(a, gt, nxt);
+                load_tile_rows<GT>(a, gt, nxt);
         });
         item = next;
         cur = nxt;
@@ -1318,17 +1338,20 @@ cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
     return cudaGetLastError();
 }
 
-int64_t pull_tiles(const Csr &g, int32_t K)
+int64_t pull_tiles(const Csr &g, int32_t K, bool host_z)
 {
     const int64_t units = g.nnz_main + g.n * (int64_t)row_cost(K);
-    return (units + kTileUnits - 1) / kTileUnits;
+    const int64_t tu = host_z ? tile_units<kHostGroup>() : tile_units<kDeviceGroup>();
+    return (units + tu - 1) / tu;
 }
 
 cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
-                             int64_t ntiles, cudaStream_t stream)
+                             int64_t ntiles, bool host_z, cudaStream_t stream)
 {
     k_partition<<<grid_for(ntiles + 1, 256, 1 << 30), 256, 0, stream>>>(
-        g.rowptr, g.n, K, ntiles, tile_row);
+        g.rowptr, g.n, K, ntiles,
+        host_z ? tile_units<kHostGroup>() : tile_units<kDeviceGroup>(),
+        tile_row);
     return cudaGetLastError();
 }
 
@@ -1389,16 +1412,18 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas, bool skip_hub_rows)
+                              cudaStream_t stream, int ctas, bool host_z)
 {
     if (ntiles == 0)
         return cudaSuccess;
     PullArgs a = pull_args(g, L, classes, laplacian, tile_row, ntiles, Yc,
                            counts, Z, nullptr, work, st);
-    a.hub_bits = skip_hub_rows ? g.hub_bits : nullptr;
+    a.hub_bits = host_z && g.chunks > 0 ? g.hub_bits : nullptr;
     const int K = a.cols;
     const int C = row_cost(K);
-    a.max_rows = (kTileUnits + C - 1) / C;
+    const int GT = host_z ? kHostGroup : kDeviceGroup;
+    const int units = 32 * GT;
+    a.max_rows = (units + C - 1) / C;
     const size_t rpb = align16((size_t)(a.max_rows + 2) * 4);
     // + kLineFloats + 4 cells: the offset (< kLineFloats) and the 16-byte
     // rounding of the zeroing; then 32 sink cells (one per lane) for arcs of
@@ -1408,22 +1433,31 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
     a.acc_off = (int32_t)rpb;
     a.slot_off = (int32_t)(rpb + accb);
     a.group_bytes = (int32_t)(a.slot_off + 16);
-    const size_t smem = plan_shared((size_t)kGroups * a.group_bytes, a);
+    // as many groups as their areas fit (wide rows take more), at most
+    // 1,024 threads
+    const size_t fixed = plan_shared(0, a);
+    const size_t room = (size_t)max_block_smem();
+    int groups = room > fixed ? (int)((room - fixed) / a.group_bytes) : 0;
+    if (groups > 1024 / GT)
+        groups = 1024 / GT;
+    if (groups < 1)
+        return cudaErrorInvalidConfiguration;
+    const size_t smem = plan_shared((size_t)groups * a.group_bytes, a);
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess)
         return e;
     a.cold_from = kLightColdFrom;
-    const int threads = kGroups * kGroupThreads;
+    const int threads = groups * GT;
     const bool w = weighted || laplacian;
+#define GEE_LIGHT(W, M)                                                        \
+    (host_z ? launch_persistent(k_pull_light<W, M, kHostGroup>, threads, smem, \
+                                a, stream, ctas)                               \
+            : launch_persistent(k_pull_light<W, M, kDeviceGroup>, threads,     \
+                                smem, a, stream, ctas))
     if (L > 1)
-        return w ? launch_persistent(k_pull_light<true, true>, threads, smem,
-                                     a, stream, ctas)
-                 : launch_persistent(k_pull_light<false, true>, threads, smem,
-                                     a, stream, ctas);
-    return w ? launch_persistent(k_pull_light<true, false>, threads, smem, a,
-                                 stream, ctas)
-             : launch_persistent(k_pull_light<false, false>, threads, smem, a,
-                                 stream, ctas);
+        return w ? GEE_LIGHT(true, true) : GEE_LIGHT(false, true);
+    return w ? GEE_LIGHT(true, false) : GEE_LIGHT(false, false);
+#undef GEE_LIGHT
 }
 
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,

@@ -23,11 +23,9 @@ constexpr int kMaxClasses = GEE_MAX_CLASSES;
 // arc plus max(K, 16) units per row (the row's Z write), so that every tile
 // moves about the same number of bytes.  Rows with more than kHubDegree arcs
 // are processed apart, in chunks of kHubChunk arcs.
-constexpr int kTileUnits = 4096;
+constexpr int kTileUnits = 1024;
 constexpr int kHubDegree = GEE_HUB_DEGREE;
 constexpr int kHubChunk = 2048;
-
-constexpr int kMaxTileArcs = kTileUnits + kHubDegree;
 
 // First error a kernel saw.  `index` is the smallest offending element.
 struct DevStatus {
@@ -99,6 +97,8 @@ inline int grid_for(int64_t work, int threads, int max_blocks)
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+// Dynamic shared memory one CTA may opt into on the current device.
+int max_block_smem();
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `stream` and return cudaGetLastError().
@@ -252,9 +252,9 @@ cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
                                    cudaStream_t stream);
 
 // Row-tile partition for K: tile_row[ntiles+1].
-int64_t pull_tiles(const Csr &g, int32_t K);
+int64_t pull_tiles(const Csr &g, int32_t K, bool host_z = false);
 cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
-                             int64_t ntiles, cudaStream_t stream);
+                             int64_t ntiles, bool host_z, cudaStream_t stream);
 
 // S4 + S5 (CSR form), three launches in this order on one stream:
 // light rows (every Z row of the tile range; hub rows get zeros), hub-row
@@ -266,9 +266,12 @@ cudaError_t launch_partition(const Csr &g, int32_t K, int32_t *tile_row,
 // ctas: persistent CTAs (0 = one per SM).  partials_only: k_pull_heavy
 // leaves every chunk's sums in hub_part (never writing Z) and
 // launch_hub_fixup(all_rows = true) writes every hub row -- so the two
-// pull kernels may run at the same time on disjoint SMs.  skip_hub_rows:
-// k_pull_light leaves the cells of hub rows untouched (instead of zeroing
-// them), so launch_hub_fixup(all_rows = true) may run at the same time too.
+// pull kernels may run at the same time on disjoint SMs.  host_z: Z is
+// page-locked host memory written over the host link -- k_pull_light takes
+// the larger tiles (fewer partial lines at tile ends; pull_tiles and
+// launch_partition must be given the same flag) and leaves the cells of hub
+// rows untouched instead of zeroing them, so launch_hub_fixup(all_rows =
+// true) may run at the same time too.
 cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian,
                               const int32_t *tile_row,
@@ -276,7 +279,7 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
                               cudaStream_t stream, int ctas = 0,
-                              bool skip_hub_rows = false);
+                              bool host_z = false);
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
