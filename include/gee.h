@@ -193,8 +193,11 @@ GEE_API gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
                                 const gee_options *opts, gee_stream_t stream);
 
 /* Sizes of a resident graph: nodes, edges, rows kept in the hub CSR (more
- * than GEE_HUB_DEGREE arcs), their arcs, device bytes held.  Any output
- * pointer may be NULL. */
+ * than GEE_HUB_DEGREE arcs), their arcs, device bytes held by the CSR.  The
+ * graph also keeps the row-tile split of up to 8 column counts it has been
+ * embedded with (4 * ((2s + n * max(cols, 16)) / 1024 + 2) bytes each), so
+ * later passes with the same K skip that step.  Any output pointer may be
+ * NULL. */
 GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n,
                                   int64_t *s, int64_t *hub_rows,
                                   int64_t *hub_arcs, int64_t *device_bytes);

@@ -251,7 +251,8 @@ class SideStream {
 gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                      const uint8_t *Yc, const uint32_t *counts, float *Z,
                      const DevStatus *st, cudaStream_t stream, int32_t L = 1,
-                     bool host_z = false)
+                     bool host_z = false, const int32_t *split = nullptr,
+                     int64_t split_tiles = 0)
 {
     const int32_t cols = L * K;
     if (L >= kWideMinLabels) {
@@ -279,19 +280,21 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         }
         return GEE_OK;
     }
-    const int64_t ntiles = pull_tiles(g, cols, host_z);
-    int32_t *tile_row = nullptr;
+    // the row-tile partition: the graph's kept one, else split here
+    int64_t ntiles = split_tiles;
+    const int32_t *tile_row = split;
     void *hub_part = nullptr;
     unsigned long long *work = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&work, 2 * sizeof(unsigned long long)));
-    GEE_CHECK_CUDA(ws.alloc((void **)&tile_row,
-                            sizeof(int32_t) * (ntiles + 1)));
     GEE_CHECK_CUDA(
         ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
-    {
+    if (tile_row == nullptr) {
+        ntiles = pull_tiles(g, cols, host_z);
+        int32_t *own = nullptr;
+        GEE_CHECK_CUDA(ws.alloc((void **)&own, sizeof(int32_t) * (ntiles + 1)));
         ProfScope p("k_partition", stream);
-        GEE_CHECK_CUDA(
-            launch_partition(g, cols, tile_row, ntiles, host_z, stream));
+        GEE_CHECK_CUDA(launch_partition(g, cols, own, ntiles, host_z, stream));
+        tile_row = own;
     }
     if (host_z && g.chunks > 0) {
         const int sms = sm_count();
@@ -480,6 +483,16 @@ struct gee_graph {
     std::mutex mu;
     bool lap_ready = false;
     cudaEvent_t lap_done = nullptr;
+    // row-tile partitions already computed, by Z columns and tile shape:
+    // they depend on the graph alone, so passes with the same K reuse them
+    struct TileSplit {
+        int32_t cols = 0;
+        bool host_z = false;
+        int64_t ntiles = 0;
+        int32_t *tile_row = nullptr;
+        cudaEvent_t ready = nullptr;
+    };
+    std::vector<TileSplit> splits;
 };
 
 namespace {
@@ -497,6 +510,47 @@ gee_status ensure_laplacian(gee_graph *g, cudaStream_t stream)
         g->lap_ready = true;
     }
     GEE_CHECK_CUDA(cudaStreamWaitEvent(stream, g->lap_done, 0));
+    return GEE_OK;
+}
+
+constexpr size_t kMaxSplits = 8;
+
+// The graph's row-tile partition for `cols` Z columns, computed on first
+// use (on `stream`, which later users wait for); null (the pass splits
+// its own) once kMaxSplits partitions are kept.
+gee_status tile_split(gee_graph *g, int32_t cols, bool host_z,
+                      cudaStream_t stream, const int32_t **tile_row,
+                      int64_t *ntiles)
+{
+    *tile_row = nullptr;
+    *ntiles = 0;
+    std::lock_guard<std::mutex> lock(g->mu);
+    for (const gee_graph::TileSplit &t : g->splits)
+        if (t.cols == cols && t.host_z == host_z) {
+            GEE_CHECK_CUDA(cudaStreamWaitEvent(stream, t.ready, 0));
+            *tile_row = t.tile_row;
+            *ntiles = t.ntiles;
+            return GEE_OK;
+        }
+    if (g->splits.size() >= kMaxSplits)
+        return GEE_OK;
+    gee_graph::TileSplit t;
+    t.cols = cols;
+    t.host_z = host_z;
+    t.ntiles = pull_tiles(g->csr, cols, host_z);
+    GraphAllocator keep(&g->owned);
+    GEE_CHECK_CUDA(keep.alloc((void **)&t.tile_row,
+                              sizeof(int32_t) * (t.ntiles + 1)));
+    GEE_CHECK_CUDA(cudaEventCreateWithFlags(&t.ready, cudaEventDisableTiming));
+    g->splits.push_back(t);  // the event is destroyed with the graph
+    {
+        ProfScope p("k_partition", stream);
+        GEE_CHECK_CUDA(launch_partition(g->csr, cols, t.tile_row, t.ntiles,
+                                        host_z, stream));
+    }
+    GEE_CHECK_CUDA(cudaEventRecord(t.ready, stream));
+    *tile_row = t.tile_row;
+    *ntiles = t.ntiles;
     return GEE_OK;
 }
 
@@ -534,8 +588,15 @@ gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
     if (rc != GEE_OK)
         return rc;
     *st_out = st;
+    const int32_t *tile_row = nullptr;
+    int64_t ntiles = 0;
+    if (L < kWideMinLabels) {
+        rc = tile_split(graph, L * K, host_z, stream, &tile_row, &ntiles);
+        if (rc != GEE_OK)
+            return rc;
+    }
     return pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
-                     stream, L, host_z);
+                     stream, L, host_z, tile_row, ntiles);
 }
 
 namespace {
@@ -733,6 +794,9 @@ void gee_graph_destroy(gee_graph *graph)
         cudaFree(p);
     if (graph->lap_done)
         cudaEventDestroy(graph->lap_done);
+    for (const gee_graph::TileSplit &t : graph->splits)
+        if (t.ready)
+            cudaEventDestroy(t.ready);
     cudaSetDevice(prev);
     delete graph;
 }

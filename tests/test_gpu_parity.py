@@ -367,3 +367,21 @@ def test_graph_host_direct_write_hub_rows_and_offsets(gee, rmat16, K, variant):
                                   f"host {variant} K={K} shift={shift}")
         rest = torch.cat([buf[:shift], buf[shift + n * K:]])
         assert torch.all(torch.isnan(rest)), shift
+
+
+def test_kept_tile_splits_many_column_counts(gee, rmat16):
+    """A resident graph keeps the row-tile split of the first 8 column
+    counts it is embedded with and splits per call after that: twelve K in
+    turn (device and page-locked host Z, which split differently), then the
+    first ones again from the kept splits -- each equal to the oracle."""
+    import torch
+    edges, n = rmat16
+    with gee.Graph(_dev(edges), n) as g:
+        for rnd in range(2):
+            for K in range(1, 13) if rnd == 0 else (1, 2, 3):
+                Y = graphgen.labels(n, K, seed=300 + 17 * K + rnd, frac_unlabeled=0.2)
+                want = oracle.embed_counts32(edges, Y, K)
+                assert np.array_equal(g.embed(_dev(Y), K).cpu().numpy(), want), (rnd, K)
+                Zp = torch.empty((n, K), dtype=torch.float32).pin_memory()
+                g.embed_host(torch.from_numpy(Y).pin_memory(), K, out=Zp)
+                assert np.array_equal(Zp.numpy(), want), (rnd, K)
