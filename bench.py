@@ -784,11 +784,14 @@ def run_precision(args, w, world, rank, local):
         _errors(gee.embed(ed, yd, K, weights=wd, strategy="atomic").cpu().numpy(), z64w))
     add("tiny SBM + weights (0,1]", "FP32 weight sums (segmented)",
         _errors(gee.embed(ed, yd, K, weights=wd, strategy="segmented").cpu().numpy(), z64w))
+    add("tiny SBM + weights (0,1]", "fixed-point sums, FP64 division (deterministic)",
+        _errors(gee.embed(ed, yd, K, weights=wd, deterministic=True).cpu().numpy(), z64w))
     z64l = oracle.embed(e, Y, K, weights=wt, laplacian=True)
     add("tiny SBM + weights (0,1]", "FP32 Laplacian (FP64 degree scale)",
         _errors(gee.embed(ed, yd, K, weights=wd, laplacian=True).cpu().numpy(), z64l))
 
-    def sampled(config, edges_h, wts_h, Ys, K, graph, n, laplacian=False, multi=False):
+    def sampled(config, edges_h, wts_h, Ys, K, graph, n, laplacian=False, multi=False,
+                deterministic=False):
         """Rows: the 64 highest-degree nodes and random ones."""
         deg = np.bincount(edges_h.ravel(), minlength=n)
         rows = np.unique(np.concatenate([np.argsort(deg)[-64:],
@@ -801,7 +804,7 @@ def run_precision(args, w, world, rank, local):
                     _errors(Z[r, l * K:(l + 1) * K], z64r), rows_checked=int(r.size))
             return
         Yd = torch.from_numpy(Ys).to(dev)
-        Z = graph.embed(Yd, K, laplacian=laplacian).cpu().numpy()
+        Z = graph.embed(Yd, K, laplacian=laplacian, deterministic=deterministic).cpu().numpy()
         if wts_h is None and not laplacian:
             r, z64r, C = oracle.embed_rows(edges_h, Ys, K, rows, with_counts=True)
             nk = oracle.class_counts(Ys, K)
@@ -809,9 +812,12 @@ def run_precision(args, w, world, rank, local):
                 _errors(Z[r], z64r, oracle.round_counts(C, nk)), rows_checked=int(r.size))
         else:
             r, z64r = oracle.embed_rows(edges_h, Ys, K, rows, weights=wts_h, laplacian=laplacian)
-            add(config, "FP32 Laplacian (resident graph)" if laplacian
-                else "FP32 weight sums (resident graph)",
-                _errors(Z[r], z64r), rows_checked=int(r.size))
+            path = "FP32 Laplacian (resident graph)" if laplacian \
+                else "FP32 weight sums (resident graph)"
+            if deterministic:
+                path = ("fixed-point Laplacian sums" if laplacian else "fixed-point sums") + \
+                    ", FP64 division (resident graph, deterministic)"
+            add(config, path, _errors(Z[r], z64r), rows_checked=int(r.size))
 
     # R-MAT scale 24 weighted (and the same graph with unit weights)
     W = WORKLOADS["rmat24"]
@@ -823,6 +829,9 @@ def run_precision(args, w, world, rank, local):
     with gee.Graph(ed, n, weights=wd) as g:
         sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n)
         sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n, laplacian=True)
+        sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n, deterministic=True)
+        sampled("R-MAT scale 24, weights (0,1]", e_h, w_h, Y_h, K, g, n, laplacian=True,
+                deterministic=True)
         Ys = np.stack([graphgen.labels(n, K, seed=900 + l, frac_unlabeled=0.1) for l in range(32)])
         sampled("R-MAT scale 24, weights (0,1], L=32", e_h, w_h, Ys, K, g, n, multi=True)
     with gee.Graph(ed, n) as g:

@@ -105,10 +105,26 @@ typedef struct gee_options {
                                   shared-memory limit) */
     int32_t block;             /* threads per CTA of the ATOMIC/PRIVATE pass
                                   (0 = 256; multiple of 32, <= 1024) */
-    int32_t reserved;
+    int32_t deterministic;     /* 1: bitwise reproducible float sums.  Each
+                                  weighted or Laplacian arc value is added as
+                                  a 64-bit fixed-point integer (units of 2^-S,
+                                  S = floor(62 - log2(longest row's arcs x
+                                  bound)), bound = max |w|, or 1 for Laplacian
+                                  values) and each cell is divided by n_k
+                                  once in FP64, so results depend neither on
+                                  the order of the additions nor on the arc
+                                  order of a rebuilt graph; every arc value is
+                                  rounded to a multiple of 2^-S.  Resident-
+                                  graph passes and SEGMENTED edge-list calls
+                                  (AUTO then picks SEGMENTED); with ATOMIC or
+                                  PRIVATE, with 8 or more label vectors of a
+                                  weighted graph and in gee_embed_batch for
+                                  weighted problems: GEE_ERR_UNSUPPORTED.
+                                  Unit weights are exact counts either way. */
 } gee_options;
 
-/* Fills *opts with the defaults (AUTO, validate_edges = 1). */
+/* Fills *opts with the defaults (AUTO, validate_edges = 1,
+ * deterministic = 0). */
 GEE_API void gee_options_default(gee_options *opts);
 
 /* Human-readable name of a status code (static string). */

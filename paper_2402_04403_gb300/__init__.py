@@ -109,14 +109,16 @@ def workspace_bytes(s, n, K, weighted=False, laplacian=False, strategy="auto") -
 
 def embed(edges, Y, K: int, weights=None, laplacian: bool = False, *,
           strategy="auto", validate_edges: bool = True, block: int = 0,
-          private_max_cells: int = 0, out=None, stream=None):
-    """Z = A W for a device edge list (gee_embed)."""
+          private_max_cells: int = 0, deterministic: bool = False, out=None,
+          stream=None):
+    """Z = A W for a device edge list (gee_embed).  deterministic: float
+    sums in fixed point, bitwise reproducible (the SEGMENTED form)."""
     torch = _torch()
     s = _edges_shape(edges)
     n = Y.numel()
     if out is None:
         out = torch.empty((n, K), dtype=torch.float32, device=Y.device)
-    o = options(strategy, validate_edges, private_max_cells, block)
+    o = options(strategy, validate_edges, private_max_cells, block, deterministic)
     rc = lib().gee_embed(
         _dev_ptr(edges, torch.int32, "edges"),
         _dev_ptr(weights, torch.float32, "weights", (s,)),
@@ -246,7 +248,8 @@ def _host_buf(a):
 
 
 def embed_host(edges, Y, K: int, weights=None, laplacian: bool = False, *,
-               strategy="auto", validate_edges: bool = True, out=None, stream=None):
+               strategy="auto", validate_edges: bool = True,
+               deterministic: bool = False, out=None, stream=None):
     """gee_embed_host: host (numpy or pinned CPU tensor) inputs and output;
     the library copies them to and from the device."""
     import numpy as np
@@ -256,7 +259,7 @@ def embed_host(edges, Y, K: int, weights=None, laplacian: bool = False, *,
     if out is None:
         out = np.empty((n, K), dtype=np.float32)
     outv = _host_buf(out)
-    o = options(strategy, validate_edges)
+    o = options(strategy, validate_edges, deterministic=deterministic)
     rc = lib().gee_embed_host(
         _host_ptr(edges, np.int32, "edges", (s, 2)),
         _host_ptr(weights, np.float32, "weights", (s,)), s,
@@ -298,11 +301,14 @@ class Graph:
         return dict(zip(("n", "s", "hub_rows", "hub_arcs", "device_bytes"),
                         (v.value for v in vals)))
 
-    def embed(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+    def embed(self, Y, K: int, laplacian: bool = False, *, deterministic: bool = False,
+              out=None, stream=None):
+        """gee_embed_graph; deterministic: float sums in fixed point,
+        bitwise reproducible."""
         torch = _torch()
         if out is None:
             out = torch.empty((self.n, K), dtype=torch.float32, device=Y.device)
-        o = options()
+        o = options(deterministic=deterministic)
         rc = lib().gee_embed_graph(
             self.handle, _dev_ptr(Y, torch.int32, "Y", (self.n,)), int(K),
             int(bool(laplacian)), _dev_ptr(out, torch.float32, "out", (self.n, K)),
@@ -310,7 +316,8 @@ class Graph:
         check(rc, "gee_embed_graph")
         return out
 
-    def embed_multi(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+    def embed_multi(self, Y, K: int, laplacian: bool = False, *, deterministic: bool = False,
+                    out=None, stream=None):
         """L label vectors (Y: int32 (L, n)) in one pass; returns Z of shape
         (n, L*K) with columns [l*K, (l+1)*K) for vector l
         (gee_embed_graph_multi)."""
@@ -320,7 +327,7 @@ class Graph:
         L = Y.shape[0]
         if out is None:
             out = torch.empty((self.n, L * K), dtype=torch.float32, device=Y.device)
-        o = options()
+        o = options(deterministic=deterministic)
         rc = lib().gee_embed_graph_multi(
             self.handle, _dev_ptr(Y, torch.int32, "Y"), int(L), int(K),
             int(bool(laplacian)), _dev_ptr(out, torch.float32, "out", (self.n, L * K)),
@@ -345,13 +352,14 @@ class Graph:
         check(rc, "gee_unsupervised")
         return Y, out, rounds.value, moved[:rounds.value].tolist()
 
-    def embed_host(self, Y, K: int, laplacian: bool = False, *, out=None, stream=None):
+    def embed_host(self, Y, K: int, laplacian: bool = False, *, deterministic: bool = False,
+                   out=None, stream=None):
         import numpy as np
         Yv = _host_buf(Y)
         if out is None:
             out = np.empty((self.n, K), dtype=np.float32)
         outv = _host_buf(out)
-        o = options()
+        o = options(deterministic=deterministic)
         rc = lib().gee_embed_graph_host(
             self.handle, _host_ptr(Yv, np.int32, "Y", (self.n,)), int(K),
             int(bool(laplacian)), _host_ptr(outv, np.float32, "out", (self.n, K)),

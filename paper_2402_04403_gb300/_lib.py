@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
         ("validate_edges", ctypes.c_int32),
         ("private_max_cells", ctypes.c_int64),
         ("block", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("deterministic", ctypes.c_int32),
     ]
 
 
@@ -184,11 +184,13 @@ def check(code: int, what: str = "") -> None:
         raise GeeError(code, what)
 
 
-def options(strategy="auto", validate_edges=True, private_max_cells=0, block=0):
+def options(strategy="auto", validate_edges=True, private_max_cells=0, block=0,
+            deterministic=False):
     o = Options()
     lib().gee_options_default(ctypes.byref(o))
     o.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
     o.validate_edges = 1 if validate_edges else 0
     o.private_max_cells = int(private_max_cells)
     o.block = int(block)
+    o.deterministic = 1 if deterministic else 0
     return o

@@ -112,6 +112,19 @@ gee_status read_status(const DevStatus *st, cudaStream_t stream)
     return static_cast<gee_status>(h.code);
 }
 
+// Deterministic float sums need the pull form (fixed-point cells owned by
+// one row tile or hub chunk): AUTO becomes SEGMENTED; the scatter forms
+// (global float atomics) cannot give them.
+gee_status deterministic_strategy(gee_options &o, bool weighted,
+                                  int32_t laplacian)
+{
+    if (!o.deterministic || !(weighted || laplacian))
+        return GEE_OK;
+    if (o.strategy == GEE_AUTO)
+        o.strategy = GEE_SEGMENTED;
+    return o.strategy == GEE_SEGMENTED ? GEE_OK : GEE_ERR_UNSUPPORTED;
+}
+
 gee_options resolve_options(const gee_options *opts)
 {
     gee_options o;
@@ -252,15 +265,20 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
                      const uint8_t *Yc, const uint32_t *counts, float *Z,
                      const DevStatus *st, cudaStream_t stream, int32_t L = 1,
                      bool host_z = false, const int32_t *split = nullptr,
-                     int64_t split_tiles = 0)
+                     int64_t split_tiles = 0, bool fixed = false)
 {
+    // fixed: weighted arc values are added as 64-bit fixed-point integers
+    const int shift = fixed ? fixed_shift(g, laplacian) : 0;
+    const size_t part_cell = fixed ? 8 : 4;
     const int32_t cols = L * K;
     if (L >= kWideMinLabels) {
+        if (fixed)
+            return GEE_ERR_UNSUPPORTED;
         unsigned long long *work = nullptr;
         void *hub_part = nullptr;
         GEE_CHECK_CUDA(ws.alloc((void **)&work, sizeof(unsigned long long)));
         GEE_CHECK_CUDA(
-            ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
+            ws.alloc(&hub_part, part_cell * (g.chunks * cols + 1)));
         {
             ProfScope p("k_wide_rows", stream);
             GEE_CHECK_CUDA(launch_wide_rows(g, L, K, g.weighted, laplacian, Yc,
@@ -287,7 +305,7 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
     unsigned long long *work = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&work, 2 * sizeof(unsigned long long)));
     GEE_CHECK_CUDA(
-        ws.alloc(&hub_part, sizeof(uint32_t) * (g.chunks * cols + 1)));
+        ws.alloc(&hub_part, part_cell * (g.chunks * cols + 1)));
     if (tile_row == nullptr) {
         ntiles = pull_tiles(g, cols, host_z);
         int32_t *own = nullptr;
@@ -309,20 +327,20 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
             GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
                                              counts, Z, hub_part, true, work + 1,
                                              st, side.stream(),
-                                             sms - light_ctas));
+                                             sms - light_ctas, fixed, shift));
         }
         {
             ProfScope p("k_hub_fixup", side.stream());
             GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian,
                                             counts, Z, hub_part, true, st,
-                                            side.stream()));
+                                            side.stream(), fixed, shift));
         }
         {
             ProfScope p("k_pull_light", stream);
             GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
                                              tile_row, ntiles, Yc, counts, Z,
                                              work, st, stream, light_ctas,
-                                             true));
+                                             true, fixed, shift));
         }
         GEE_CHECK_CUDA(side.join());
         return GEE_OK;
@@ -331,18 +349,20 @@ gee_status pull_step(Workspace &ws, const Csr &g, int32_t K, bool laplacian,
         ProfScope p("k_pull_light", stream);
         GEE_CHECK_CUDA(launch_pull_light(g, L, K, g.weighted, laplacian,
                                          tile_row, ntiles, Yc, counts, Z,
-                                         work, st, stream, 0, host_z));
+                                         work, st, stream, 0, host_z, fixed,
+                                         shift));
     }
     if (g.chunks > 0) {
         ProfScope p("k_pull_heavy", stream);
         GEE_CHECK_CUDA(launch_pull_heavy(g, L, K, g.weighted, laplacian, Yc,
                                          counts, Z, hub_part, false, work + 1,
-                                         st, stream));
+                                         st, stream, 0, fixed, shift));
     }
     if (g.hubs > 0) {
         ProfScope p("k_hub_fixup", stream);
         GEE_CHECK_CUDA(launch_hub_fixup(g, cols, g.weighted, laplacian, counts,
-                                        Z, hub_part, false, st, stream));
+                                        Z, hub_part, false, st, stream, fixed,
+                                        shift));
     }
     return GEE_OK;
 }
@@ -382,7 +402,9 @@ gee_status embed_coo(Workspace &ws, const int32_t *E, const float *w,
                 return GEE_ERR_INVALID_ARG;
             GEE_CHECK_CUDA(build_laplacian_values(g, ws, ws, stream));
         }
-        return pull_step(ws, g, K, laplacian != 0, Yc, counts, Z, st, stream);
+        return pull_step(ws, g, K, laplacian != 0, Yc, counts, Z, st, stream,
+                         1, false, nullptr, 0,
+                         o.deterministic != 0 && (w != nullptr || laplacian));
     }
     rc = labels_launch(Y, n, K, nullptr, Yc, counts, st, stream);
     if (rc != GEE_OK)
@@ -562,8 +584,13 @@ gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                                    const int32_t *Y, int32_t L, int32_t K,
                                    int32_t laplacian, float *Z,
                                    DevStatus **st_out, cudaStream_t stream,
-                                   bool host_z)
+                                   bool host_z, bool deterministic)
 {
+    // bit-reproducible float sums: fixed-point accumulation (single pass
+    // forms); counts are exact already
+    const bool fixed = deterministic && (graph->csr.weighted || laplacian);
+    if (fixed && L >= kWideMinLabels)
+        return GEE_ERR_UNSUPPORTED;
     if (laplacian) {
         gee_status rc = ensure_laplacian(graph, stream);
         if (rc != GEE_OK)
@@ -596,7 +623,7 @@ gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
             return rc;
     }
     return pull_step(ws, graph->csr, K, laplacian != 0, Yc, counts, Z, st,
-                     stream, L, host_z, tile_row, ntiles);
+                     stream, L, host_z, tile_row, ntiles, fixed);
 }
 
 namespace {
@@ -604,11 +631,11 @@ namespace {
 gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
                            int32_t K, int32_t laplacian, float *Z,
                            cudaStream_t stream, int32_t L = 1,
-                           bool host_z = false)
+                           bool host_z = false, bool deterministic = false)
 {
     DevStatus *st = nullptr;
     gee_status rc = graph_pass_enqueue(ws, graph, Y, L, K, laplacian, Z, &st,
-                                       stream, host_z);
+                                       stream, host_z, deterministic);
     if (rc != GEE_OK)
         return rc;
     return read_status(st, stream);
@@ -626,7 +653,7 @@ void gee_options_default(gee_options *opts)
     opts->validate_edges = 1;
     opts->private_max_cells = 0;
     opts->block = 0;
-    opts->reserved = 0;
+    opts->deterministic = 0;
 }
 
 const char *gee_status_string(gee_status status)
@@ -730,9 +757,13 @@ gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
         return GEE_ERR_NODE_RANGE;
     if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
         return GEE_ERR_INVALID_ARG;
+    gee_options oo = o;
+    rc = deterministic_strategy(oo, weights != nullptr, laplacian);
+    if (rc != GEE_OK)
+        return rc;
     Workspace ws(stream);
     DevStatus *st = nullptr;
-    rc = embed_coo(ws, edges, weights, s, Y, n, K, laplacian, Z, o, stream,
+    rc = embed_coo(ws, edges, weights, s, Y, n, K, laplacian, Z, oo, stream,
                    &st);
     if (rc != GEE_OK)
         return rc;
@@ -745,7 +776,7 @@ gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
                           const gee_options *opts, gee_stream_t stream_)
 {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    const gee_options o = resolve_options(opts);
+    gee_options o = resolve_options(opts);
     gee_status rc = check_common(s, n, K, o.block);
     if (rc != GEE_OK)
         return rc;
@@ -754,6 +785,11 @@ gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
+    if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
+        return GEE_ERR_INVALID_ARG;
+    rc = deterministic_strategy(o, weights_h != nullptr, laplacian);
+    if (rc != GEE_OK)
+        return rc;
     Workspace ws(stream);
     int32_t *E = nullptr, *Y = nullptr;
     float *w = nullptr, *Z = nullptr;
@@ -821,6 +857,8 @@ gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
             rc = GEE_ERR_INVALID_ARG;
         if (rc == GEE_OK && q.s > 0 && q.n == 0)
             rc = GEE_ERR_NODE_RANGE;
+        if (rc == GEE_OK && o.deterministic && q.weights != nullptr)
+            rc = GEE_ERR_UNSUPPORTED;  // batches add floats in global atomics
         if (rc != GEE_OK) {
             if (statuses != nullptr)
                 statuses[i] = rc;
@@ -962,7 +1000,8 @@ gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
         words_misaligned(Y, Z))
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
-    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
+    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, 1, false,
+                           o.deterministic != 0);
 }
 
 gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
@@ -983,7 +1022,8 @@ gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
         words_misaligned(Y, Z))
         return GEE_ERR_INVALID_ARG;
     Workspace ws(stream);
-    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, L);
+    return embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, L, false,
+                           o.deterministic != 0);
 }
 
 gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
@@ -1011,10 +1051,11 @@ gee_status gee_embed_graph_host(gee_graph *graph, const int32_t *Y_h,
     float *Zdirect = mapped_host(Z_h);
     if (Zdirect != nullptr)
         return embed_graph_dev(ws, graph, Y, K, laplacian, Zdirect, stream, 1,
-                               true);
+                               true, o.deterministic != 0);
     float *Z = nullptr;
     GEE_CHECK_CUDA(ws.alloc((void **)&Z, sizeof(float) * (n * K + 1)));
-    rc = embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream);
+    rc = embed_graph_dev(ws, graph, Y, K, laplacian, Z, stream, 1, false,
+                         o.deterministic != 0);
     if (rc != GEE_OK)
         return rc;
     GEE_CHECK_CUDA(cudaMemcpyAsync(Z_h, Z, sizeof(float) * n * K,

@@ -23,6 +23,9 @@
 // No global atomics touch Z: every light row is written once; a hub row
 // gets zeros from k_pull_light, then its value from k_pull_heavy or
 // k_hub_fixup, which run after it on the same stream.
+#include <cmath>
+#include <cstring>
+
 #include "gee_internal.cuh"
 
 namespace gee {
@@ -598,6 +601,7 @@ struct PullArgs {
                              // ranks [0, hot_n), a multiple of 16
     int32_t cold_from;       // labels of ranks >= cold_from are read past L1
     int32_t copies;          // heavy kernel: accumulator copies per warp
+    double fx_scale, fx_inv; // fixed-point arc values: 2^shift, 2^-shift
     const uint32_t *hub_bits;  // light kernel: if set, hub rows' cells are
                                // left untouched (bit r: row r is a hub row)
     int32_t hub_direct;      // 1: single-chunk hub rows are written to Z by
@@ -712,7 +716,8 @@ struct TileCells {
 // and single arcs for the head and tail.  cells maps (arc, label) to an
 // accumulator index; arcs whose label is unknown go to this thread's own
 // sink cell (no branch, no shared-address contention).
-template <bool WEIGHTED, bool MULTI, int NT, class Cells, int UNROLL = kUnroll>
+template <bool WEIGHTED, bool MULTI, int NT, class Cells, int UNROLL = kUnroll,
+          bool FIXED = false>
 __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            const int32_t *colp,
                                            const float *valp, int NA, int t,
@@ -722,8 +727,12 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            int hot_n = 0)
 {
     float *accf = reinterpret_cast<float *>(acc);
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
     auto put = [&](int c, float w) {
-        if (WEIGHTED)
+        if (FIXED)  // 8-byte cells: the arc value in fixed point
+            atomicAdd(acc64 + c, (unsigned long long)__double2ll_rn(
+                                     (double)w * a.fx_scale));
+        else if (WEIGHTED)
             atomicAdd(accf + c, w);
         else
             atomicAdd(acc + c, 1u);
@@ -868,7 +877,7 @@ __device__ __forceinline__ void load_tile_rows(const PullArgs &a, int gt,
 // barrier): sweep its arcs into the accumulators, barrier, then scale and
 // write its Z rows.  `before_write` runs between the barrier and the write
 // phase (the caller issues the next tile's loads there).
-template <bool WEIGHTED, bool MULTI, int GT, class BeforeWrite>
+template <bool WEIGHTED, bool MULTI, int GT, bool FIXED, class BeforeWrite>
 __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
                                          unsigned char *gs,
                                          const uint32_t *nk,
@@ -890,7 +899,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     // sweep: the row of arc i is the last row starting at or before i
     if (NA > 0) {
         TileCells tc{rp, NR, K, off, 0, 0};
-        sweep_arcs<WEIGHTED, MULTI, GT, TileCells, kLightUnroll>(
+        sweep_arcs<WEIGHTED, MULTI, GT, TileCells, kLightUnroll, FIXED>(
             a, a.col + tr.A0, WEIGHTED ? a.val + tr.A0 : nullptr, NA, gt, acc,
             a.max_rows * K + kLineFloats + 4 + (gt & 31), tc);
     }
@@ -909,10 +918,30 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     const int tail0 = head + 4 * nq;
     // each cell read here is cleared again, so the accumulators are zero
     // for the group's next tile
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
     auto quad_values = [&](int j0) {
+        float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if constexpr (FIXED) {  // four 8-byte cells
+            ulonglong2 *p2 = reinterpret_cast<ulonglong2 *>(acc64 + off + j0);
+            const ulonglong2 c0 = p2[0], c1 = p2[1];
+            if ((c0.x | c0.y | c1.x | c1.y) != 0ull) {
+                p2[0] = make_ulonglong2(0ull, 0ull);
+                p2[1] = make_ulonglong2(0ull, 0ull);
+                int k = class_of(a, j0);
+                const unsigned long long cs[4] = {c0.x, c0.y, c1.x, c1.y};
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    o[e] = fixed_to_z(cs[e], a.fx_inv, nk[k]);
+                    if (++k == K)
+                        k = 0;
+                }
+                o4 = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            return o4;
+        }
         uint4 *p4 = reinterpret_cast<uint4 *>(acc + off + j0);
         const uint4 c4 = *p4;
-        float4 o4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
             *p4 = make_uint4(0u, 0u, 0u, 0u);
             int k = class_of(a, j0);
@@ -929,6 +958,11 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
         return o4;
     };
     auto scalar_value = [&](int j) {
+        if constexpr (FIXED) {
+            const unsigned long long c = acc64[off + j];
+            acc64[off + j] = 0ull;
+            return fixed_to_z(c, a.fx_inv, nk[class_of(a, j)]);
+        }
         const uint32_t c = acc[off + j];
         acc[off + j] = 0u;
         return cell_value<WEIGHTED>(c, class_of(a, j), nk, table);
@@ -989,7 +1023,7 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
 // clears before this tile's sweep), accumulators complete.  The setup
 // rewrites only the row starts, which no thread reads after the second
 // barrier.
-template <bool WEIGHTED, bool MULTI, int GT>
+template <bool WEIGHTED, bool MULTI, int GT, bool FIXED>
 __global__ void __launch_bounds__(1024, 1)
     k_pull_light(PullArgs a)
 {
@@ -1010,8 +1044,8 @@ __global__ void __launch_bounds__(1024, 1)
     {
         // every cell a tile can use: max_rows rows at a line offset
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        const int quads = (a.max_rows * K + kLineFloats + 3) / 4;
-        for (int c = gt; c < quads; c += GT)
+        const int words = (a.max_rows * K + kLineFloats + 3) / 4 * (FIXED ? 2 : 1);
+        for (int c = gt; c < words; c += GT)
             acc4[c] = make_uint4(0u, 0u, 0u, 0u);
     }
 
@@ -1044,7 +1078,7 @@ __global__ void __launch_bounds__(1024, 1)
             nxt.r0 = a.tile_row[next];
             nxt.r1 = a.tile_row[next + 1];
         }
-        row_tile<WEIGHTED, MULTI, GT>(a, g, gt, gs, nk, table, cur, [&]() {
+        row_tile<WEIGHTED, MULTI, GT, FIXED>(a, g, gt, gs, nk, table, cur, [&]() {
             if (next < a.ntiles)  // in flight during the write phase
                 load_tile_rows<GT>(a, gt, nxt);
         });
@@ -1053,7 +1087,7 @@ __global__ void __launch_bounds__(1024, 1)
     }
 }
 
-template <bool WEIGHTED, bool MULTI>
+template <bool WEIGHTED, bool MULTI, bool FIXED>
 __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -1075,6 +1109,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     uint32_t *acc = reinterpret_cast<uint32_t *>(sm + a.area_off +
                                                  (size_t)wib * a.group_bytes);
     float *accf = reinterpret_cast<float *>(acc);
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
     const int copies = WEIGHTED ? a.copies : 1;  // a power of two
     const int copy = (lane & (copies - 1)) * K;
     // warps draw kChunkGrab consecutive chunks at a time from a counter
@@ -1088,22 +1123,36 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         const int64_t c_lo = (int64_t)g0;
         const int64_t c_hi = min(c_lo + kChunkGrab, a.chunks);
     for (int64_t c = c_lo; c < c_hi; ++c) {
-        for (int i = lane; i < copies * K; i += 32)
-            acc[i] = 0u;
+        for (int i = lane; i < copies * K; i += 32) {
+            if (FIXED)
+                acc64[i] = 0ull;
+            else
+                acc[i] = 0u;
+        }
         __syncwarp();
         const int32_t h = a.chunk_hub[c];
         const int64_t b = a.chunk_begin[c];
         const int64_t hend = a.hub_ptr[h + 1];
         const int n = (int)((b + kHubChunk < hend ? b + kHubChunk : hend) - b);
         ChunkCells cells{copy};
-        sweep_arcs<WEIGHTED, MULTI, 32>(a, a.col_h + b,
-                                 WEIGHTED ? a.val_h + b : nullptr, n, lane,
-                                 acc, copies * K + lane, cells, hot, hot_n);
+        sweep_arcs<WEIGHTED, MULTI, 32, ChunkCells, kUnroll, FIXED>(
+            a, a.col_h + b, WEIGHTED ? a.val_h + b : nullptr, n, lane, acc,
+            copies * K + lane, cells, hot, hot_n);
         __syncwarp();
         const bool whole =
             a.hub_direct && a.hub_chunk0[h + 1] - a.hub_chunk0[h] == 1;
         float *zrow = a.Z + (int64_t)a.hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
+            if (FIXED) {  // exact integer sums: any order
+                unsigned long long q = 0ull;
+                for (int r = 0; r < copies; ++r)
+                    q += acc64[r * K + k];
+                if (whole)
+                    zrow[k] = fixed_to_z(q, a.fx_inv, nk[k]);
+                else
+                    reinterpret_cast<unsigned long long *>(a.hub_part)[c * K + k] = q;
+                continue;
+            }
             uint32_t bits;
             if (WEIGHTED) {
                 float s = 0.0f;
@@ -1129,13 +1178,13 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
 // One warp per hub row: its chunk partials summed in chunk order, then
 // scaled.  Rows with fewer than min_chunks chunks are skipped (1: every hub
 // row; 2: single-chunk rows were written by k_pull_heavy).
-template <bool WEIGHTED>
+template <bool WEIGHTED, bool FIXED>
 __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
                             const int32_t *__restrict__ hub_chunk0,
                             int64_t hubs, const uint32_t *__restrict__ part,
                             const uint32_t *__restrict__ counts, int32_t K,
                             float *__restrict__ Z, int32_t min_chunks,
-                            const DevStatus *st)
+                            double fx_inv, const DevStatus *st)
 {
     if (failed(st))
         return;
@@ -1148,7 +1197,14 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
             continue;
         float *zrow = Z + (int64_t)hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
-            if (WEIGHTED) {
+            if (FIXED) {
+                const unsigned long long *p64 =
+                    reinterpret_cast<const unsigned long long *>(part);
+                unsigned long long q = 0ull;
+                for (int32_t c = c0; c < c1; ++c)
+                    q += p64[(int64_t)c * K + k];
+                zrow[k] = fixed_to_z(q, fx_inv, counts[k]);
+            } else if (WEIGHTED) {
                 float s = 0.0f;
                 for (int32_t c = c0; c < c1; ++c)
                     s += __uint_as_float(part[(int64_t)c * K + k]);
@@ -1175,7 +1231,39 @@ size_t plan_shared(size_t area_bytes, PullArgs &a)
     return fixed + area_bytes;
 }
 
+// ext[0] = max degree, ext[1] = bits of max |w| (non-negative floats order
+// like their bit patterns).
+__global__ void k_graph_extent(const uint32_t *__restrict__ deg, int64_t n,
+                               const float *__restrict__ w, int64_t s,
+                               uint32_t *__restrict__ ext)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    uint32_t d = 0u, m = 0u;
+    for (int64_t i = tid; i < n; i += nthreads)
+        d = max(d, deg[i]);
+    if (w != nullptr)
+        for (int64_t i = tid; i < s; i += nthreads)
+            m = max(m, __float_as_uint(fabsf(w[i])));
+    for (int o = 16; o > 0; o >>= 1) {
+        d = max(d, __shfl_xor_sync(0xffffffffu, d, o));
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(ext, d);
+        atomicMax(ext + 1, m);
+    }
+}
+
 }  // namespace
+
+int fixed_shift(const Csr &g, bool laplacian)
+{
+    const double bound = laplacian ? 1.0
+                         : g.max_abs_w > 0.0f ? (double)g.max_abs_w : 1.0;
+    const double m = (g.max_deg > 0 ? (double)g.max_deg : 1.0) * bound;
+    return (int)std::floor(62.0 - std::log2(m));
+}
 
 // ---------------------------------------------------------------- host side
 cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
@@ -1204,6 +1292,12 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
     if (s > 0)
         k_csr_degree<<<grid_for(s, 256, sms * 8), 256, 0, stream>>>(
             E, w, s, n, deg, st);
+    uint32_t *ext;
+    GEE_TRY(al.alloc((void **)&ext, sizeof(uint32_t) * 2));
+    GEE_TRY(cudaMemsetAsync(ext, 0, sizeof(uint32_t) * 2, stream));
+    if (n > 0 || w != nullptr)
+        k_graph_extent<<<grid_for(n > s ? n : s, 256, sms * 4), 256, 0,
+                         stream>>>(deg, n, w, w != nullptr ? s : 0, ext);
     if (n > 0)
         k_classify<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
             deg, n, deg_main, hub);
@@ -1239,8 +1333,13 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
     DevStatus hst;
     GEE_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost,
                             stream));
+    uint32_t hext[2];
+    GEE_TRY(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost,
+                            stream));
     GEE_TRY(cudaStreamSynchronize(stream));
     g.negative_weight = hst.aux;
+    g.max_deg = hext[0];
+    std::memcpy(&g.max_abs_w, &hext[1], sizeof(float));
     if (hst.code != 0)
         return cudaSuccess;  // caller reports the status
     g.nnz_main = host[0];
@@ -1415,7 +1514,8 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               int64_t ntiles, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas, bool host_z)
+                              cudaStream_t stream, int ctas, bool host_z,
+                              bool fixed, int shift)
 {
     if (ntiles == 0)
         return cudaSuccess;
@@ -1431,16 +1531,18 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
     // + kLineFloats + 4 cells: the offset (< kLineFloats) and the 16-byte
     // rounding of the zeroing; then 32 sink cells (one per lane) for arcs of
     // unknown label
-    const size_t accb =
-        align16((size_t)(a.max_rows * K + kLineFloats + 4 + 32) * 4);
+    const size_t accb = align16((size_t)(a.max_rows * K + kLineFloats + 4 + 32) *
+                                (fixed ? 8 : 4));
+    a.fx_scale = std::ldexp(1.0, shift);
+    a.fx_inv = std::ldexp(1.0, -shift);
     a.acc_off = (int32_t)rpb;
     a.slot_off = (int32_t)(rpb + accb);
     a.group_bytes = (int32_t)(a.slot_off + 16);
     // as many groups as their areas fit (wide rows take more), at most
     // 1,024 threads
-    const size_t fixed = plan_shared(0, a);
+    const size_t base = plan_shared(0, a);
     const size_t room = (size_t)max_block_smem();
-    int groups = room > fixed ? (int)((room - fixed) / a.group_bytes) : 0;
+    int groups = room > base ? (int)((room - base) / a.group_bytes) : 0;
     if (groups > 1024 / GT)
         groups = 1024 / GT;
     if (groups < 1)
@@ -1452,14 +1554,16 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
     a.cold_from = kLightColdFrom;
     const int threads = groups * GT;
     const bool w = weighted || laplacian;
-#define GEE_LIGHT(W, M)                                                        \
-    (host_z ? launch_persistent(k_pull_light<W, M, kHostGroup>, threads, smem, \
-                                a, stream, ctas)                               \
-            : launch_persistent(k_pull_light<W, M, kDeviceGroup>, threads,     \
+#define GEE_LIGHT(W, M, F)                                                     \
+    (host_z ? launch_persistent(k_pull_light<W, M, kHostGroup, F>, threads,    \
+                                smem, a, stream, ctas)                         \
+            : launch_persistent(k_pull_light<W, M, kDeviceGroup, F>, threads,  \
                                 smem, a, stream, ctas))
+    if (fixed)
+        return L > 1 ? GEE_LIGHT(true, true, true) : GEE_LIGHT(true, false, true);
     if (L > 1)
-        return w ? GEE_LIGHT(true, true) : GEE_LIGHT(false, true);
-    return w ? GEE_LIGHT(true, false) : GEE_LIGHT(false, false);
+        return w ? GEE_LIGHT(true, true, false) : GEE_LIGHT(false, true, false);
+    return w ? GEE_LIGHT(true, false, false) : GEE_LIGHT(false, false, false);
 #undef GEE_LIGHT
 }
 
@@ -1468,7 +1572,8 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               const uint32_t *counts, float *Z,
                               void *hub_part, bool partials_only,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas)
+                              cudaStream_t stream, int ctas, bool fixed,
+                              int shift)
 {
     if (g.chunks == 0)
         return cudaSuccess;
@@ -1488,41 +1593,50 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     a.copies = 1;
     while (w && a.copies < 4 && 2 * a.copies * a.cols <= kHeavyCopyCells)
         a.copies *= 2;
-    a.group_bytes = (int32_t)align16((size_t)(a.copies * a.cols + 32) * 4);
+    a.group_bytes =
+        (int32_t)align16((size_t)(a.copies * a.cols + 32) * (fixed ? 8 : 4));
+    a.fx_scale = std::ldexp(1.0, shift);
+    a.fx_inv = std::ldexp(1.0, -shift);
     a.hot_n = L > 1 ? 0 : (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
     a.cold_from = a.hot_n;
     const size_t area = (size_t)(kHeavyThreads / 32) * a.group_bytes;
     const size_t smem = plan_shared(area + (size_t)a.hot_n, a);
     a.hot_off = a.area_off + (int32_t)area;
+#define GEE_HEAVY(W, M, F)                                                     \
+    launch_persistent(k_pull_heavy<W, M, F>, kHeavyThreads, smem, a, stream,   \
+                      ctas)
+    if (fixed)
+        return L > 1 ? GEE_HEAVY(true, true, true) : GEE_HEAVY(true, false, true);
     if (L > 1)
-        return w ? launch_persistent(k_pull_heavy<true, true>, kHeavyThreads,
-                                     smem, a, stream, ctas)
-                 : launch_persistent(k_pull_heavy<false, true>, kHeavyThreads,
-                                     smem, a, stream, ctas);
-    return w ? launch_persistent(k_pull_heavy<true, false>, kHeavyThreads, smem,
-                                 a, stream, ctas)
-             : launch_persistent(k_pull_heavy<false, false>, kHeavyThreads, smem,
-                                 a, stream, ctas);
+        return w ? GEE_HEAVY(true, true, false) : GEE_HEAVY(false, true, false);
+    return w ? GEE_HEAVY(true, false, false) : GEE_HEAVY(false, false, false);
+#undef GEE_HEAVY
 }
 
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
                              const void *hub_part, bool all_rows,
-                             const DevStatus *st, cudaStream_t stream)
+                             const DevStatus *st, cudaStream_t stream,
+                             bool fixed, int shift)
 {
     if (g.hubs == 0)
         return cudaSuccess;
     const uint32_t *part = static_cast<const uint32_t *>(hub_part);
     const int fb = grid_for(g.hubs * 32, 256, sm_count() * 8);
     const int32_t min_chunks = all_rows ? 1 : 2;
-    if (weighted || laplacian)
-        k_hub_fixup<true><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
-                                                  g.hubs, part, counts, K, Z,
-                                                  min_chunks, st);
+    const double inv = std::ldexp(1.0, -shift);
+    if (fixed)
+        k_hub_fixup<true, true><<<fb, 256, 0, stream>>>(
+            g.hub_row, g.hub_chunk0, g.hubs, part, counts, K, Z, min_chunks,
+            inv, st);
+    else if (weighted || laplacian)
+        k_hub_fixup<true, false><<<fb, 256, 0, stream>>>(
+            g.hub_row, g.hub_chunk0, g.hubs, part, counts, K, Z, min_chunks,
+            inv, st);
     else
-        k_hub_fixup<false><<<fb, 256, 0, stream>>>(g.hub_row, g.hub_chunk0,
-                                                   g.hubs, part, counts, K, Z,
-                                                   min_chunks, st);
+        k_hub_fixup<false, false><<<fb, 256, 0, stream>>>(
+            g.hub_row, g.hub_chunk0, g.hubs, part, counts, K, Z, min_chunks,
+            inv, st);
     return cudaGetLastError();
 }
 

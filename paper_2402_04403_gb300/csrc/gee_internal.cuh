@@ -85,6 +85,19 @@ __device__ __forceinline__ float sum_to_z(float acc, uint32_t nk)
     return __fdiv_rn(acc, static_cast<float>(nk));
 }
 
+// Deterministic weighted cell: an exact sum of fixed-point arc values
+// (multiples of inv = 2^-shift) divided by n_k in FP64, rounded once to
+// float.  Integer sums do not depend on the order of the additions.
+__device__ __forceinline__ float fixed_to_z(unsigned long long q, double inv,
+                                            uint32_t nk)
+{
+    if (nk == 0u || q == 0ull)
+        return 0.0f;
+    return __double2float_rn(__ddiv_rn(
+        static_cast<double>(static_cast<long long>(q)) * inv,
+        static_cast<double>(nk)));
+}
+
 inline int grid_for(int64_t work, int threads, int max_blocks)
 {
     int64_t b = (work + threads - 1) / threads;
@@ -171,6 +184,8 @@ struct Csr {
     int64_t hub_arcs = 0;
     bool weighted = false;
     int32_t negative_weight = 0;
+    uint32_t max_deg = 0;       // arcs of the longest row
+    float max_abs_w = 0.0f;     // largest |weight| (weighted graphs)
     int64_t *rowptr = nullptr;      // [n+1], hub rows empty
     int32_t *rank = nullptr;        // [n] degree rank of each node
     int32_t *col = nullptr;         // [nnz_main + pad] target ranks
@@ -186,6 +201,11 @@ struct Csr {
     float *lap_val = nullptr;       // Laplacian arc values (lazy)
     float *lap_val_h = nullptr;
 };
+
+// Shift of the fixed-point form of a graph's arc values: every cell sums at
+// most max_deg values of magnitude <= bound (|w|, or 1 for Laplacian values
+// of non-negative weights), so cell sums stay below 2^62.
+int fixed_shift(const Csr &g, bool laplacian);
 
 // Allocation callback used by the CSR builder (pool or cudaMalloc).
 struct Allocator {
@@ -279,17 +299,24 @@ cudaError_t launch_pull_light(const Csr &g, int32_t L, int32_t classes,
                               const uint32_t *counts, float *Z,
                               unsigned long long *work, const DevStatus *st,
                               cudaStream_t stream, int ctas = 0,
-                              bool host_z = false);
+                              bool host_z = false, bool fixed = false,
+                              int shift = 0);
 cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
                               bool weighted, bool laplacian, const uint8_t *Yc,
                               const uint32_t *counts, float *Z,
                               void *hub_part, bool partials_only,
                               unsigned long long *work, const DevStatus *st,
-                              cudaStream_t stream, int ctas = 0);
+                              cudaStream_t stream, int ctas = 0,
+                              bool fixed = false, int shift = 0);
+// fixed (weighted passes): arc values are added as 64-bit fixed-point
+// integers with `shift` fractional bits (fixed_shift), so every cell's sum
+// is exact and independent of the order of the additions; hub_part then
+// holds 8-byte partials.
 cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
                              bool laplacian, const uint32_t *counts, float *Z,
                              const void *hub_part, bool all_rows,
-                             const DevStatus *st, cudaStream_t stream);
+                             const DevStatus *st, cudaStream_t stream,
+                             bool fixed = false, int shift = 0);
 
 // S4 + S5 (CSR form) for many label vectors (gee_wide.cu): the lanes of a
 // warp take the labels of one arc.  Same order and contract as the three
@@ -367,11 +394,14 @@ bool tuned_choice(int64_t s, int64_t n, int32_t K, gee_strategy *strategy,
 // S1-S5 of L label vectors (Y[l*n + i], L >= 1) on a resident graph,
 // enqueued on `stream` without waiting: *st receives the call's device
 // status word (in ws).  Z is [n][L*K].  Argument checks are the caller's.
+// deterministic: float sums in fixed point (bitwise reproducible); not for
+// L >= kWideMinLabels with weights (GEE_ERR_UNSUPPORTED).
 bool graph_weighted(const gee_graph *graph);
 gee_status graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                               const int32_t *Y, int32_t L, int32_t K,
                               int32_t laplacian, float *Z, DevStatus **st,
-                              cudaStream_t stream, bool host_z = false);
+                              cudaStream_t stream, bool host_z = false,
+                              bool deterministic = false);
 
 // ------------------------------------------------------------ tracing
 // When tracing is on (gee_profile_enable), a ProfScope brackets one kernel
