@@ -63,7 +63,29 @@ def test_default_options(gee):
     from paper_2402_04403_gb300 import _lib
     o = _lib.Options()
     _lib.lib().gee_options_default(ctypes.byref(o))
-    assert (o.strategy, o.validate_edges, o.private_max_cells, o.block) == (0, 1, 0, 0)
+    assert (o.strategy, o.validate_edges, o.private_max_cells, o.block,
+            o.deterministic) == (0, 1, 0, 0, 0)
+
+
+def test_deterministic_refusals_need_no_gpu(gee):
+    """Deterministic float sums need the pull form: the scatter strategies
+    and weighted batch problems are refused on the host (GEE_ERR_UNSUPPORTED
+    = 8), before any CUDA call."""
+    from paper_2402_04403_gb300 import _lib
+    lib = gee.load()
+    null = ctypes.c_void_p()
+    w = ctypes.c_void_p(256)  # a weights pointer that is never read
+    for strategy in ("atomic", "private"):
+        o = gee._lib.options(strategy, deterministic=True)
+        assert lib.gee_embed(null, w, 0, null, 0, 2, 0, null, ctypes.byref(o), null) == 8
+        assert lib.gee_embed_host(null, w, 0, null, 0, 2, 0, null, ctypes.byref(o),
+                                  null) == 8
+    arr = (_lib.Problem * 1)()
+    arr[0].weights, arr[0].K = w, 3
+    statuses = (ctypes.c_int32 * 1)()
+    o = gee._lib.options(deterministic=True)
+    assert lib.gee_embed_batch(arr, 1, statuses, ctypes.byref(o), null) == 8
+    assert statuses[0] == 8
 
 
 def test_argument_checks_return_before_any_device_work(gee):
