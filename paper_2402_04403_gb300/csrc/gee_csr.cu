@@ -1599,12 +1599,21 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     a.fx_inv = std::ldexp(1.0, -shift);
     a.hot_n = L > 1 ? 0 : (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
     a.cold_from = a.hot_n;
-    const size_t area = (size_t)(kHeavyThreads / 32) * a.group_bytes;
+    // as many warps as their accumulators fit next to the hot labels (wide
+    // rows of 8-byte cells take more than 32 would have)
+    const size_t base = plan_shared((size_t)a.hot_n, a);
+    const size_t room = (size_t)max_block_smem();
+    int warps = room > base ? (int)((room - base) / a.group_bytes) : 0;
+    if (warps > kHeavyThreads / 32)
+        warps = kHeavyThreads / 32;
+    if (warps < 1)
+        return cudaErrorInvalidConfiguration;
+    const size_t area = (size_t)warps * a.group_bytes;
     const size_t smem = plan_shared(area + (size_t)a.hot_n, a);
     a.hot_off = a.area_off + (int32_t)area;
+    const int threads = warps * 32;
 #define GEE_HEAVY(W, M, F)                                                     \
-    launch_persistent(k_pull_heavy<W, M, F>, kHeavyThreads, smem, a, stream,   \
-                      ctas)
+    launch_persistent(k_pull_heavy<W, M, F>, threads, smem, a, stream, ctas)
     if (fixed)
         return L > 1 ? GEE_HEAVY(true, true, true) : GEE_HEAVY(true, false, true);
     if (L > 1)

@@ -119,3 +119,18 @@ def test_forms_that_refuse(gee, weighted_rmat):
         # without weights the multi-label form is exact counts: accepted
     with gee.Graph(_dev(e), n) as g:
         g.embed_multi(_dev(Ys), K, deterministic=True)
+
+
+def test_wide_rows_of_fixed_point_cells(gee, weighted_rmat):
+    """4 vectors of K = 255 (1,020 columns of 8-byte cells): the kernels
+    take fewer groups / warps so their accumulators fit, and the result is
+    still each vector's own deterministic pass."""
+    n, e, w, _, _ = weighted_rmat
+    L, K = 4, 255
+    Ys = np.stack([graphgen.labels(n, K, seed=95 + l, frac_unlabeled=0.1) for l in range(L)])
+    with gee.Graph(_dev(e), n, weights=_dev(w)) as g:
+        Z = g.embed_multi(_dev(Ys), K, deterministic=True).cpu().numpy()
+        for l in (0, L - 1):
+            one = g.embed(_dev(Ys[l]), K, deterministic=True).cpu().numpy()
+            assert np.array_equal(Z[:, l * K:(l + 1) * K], one), l
+    _close_to_oracle(Z[:, :K], oracle.embed(e, Ys[0], K, weights=w))
