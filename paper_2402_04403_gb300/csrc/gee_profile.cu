@@ -4,13 +4,16 @@
 // events recorded on the stream the kernel is launched on; gee_profile_read
 // waits for them and reports launches, total and largest duration per kernel
 // name.  Used by the benchmark to time the edge-pass kernel inside a running
-// step, and to count the library's launches.
+// step, and to count the library's launches.  Every launch is also an NVTX
+// range named for its kernel, whether or not timing is enabled.
 #include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "gee_internal.cuh"
 
@@ -49,6 +52,9 @@ cudaEvent_t take_event()
 ProfScope::ProfScope(const char *name, cudaStream_t stream)
     : name_(name), stream_(stream)
 {
+    // a named host range around the launch for NVTX tools (a no-op without
+    // one attached)
+    nvtxRangePushA(name_);
     if (!g_on.load(std::memory_order_relaxed))
         return;
     // launches captured into a CUDA graph are not traced
@@ -63,6 +69,7 @@ ProfScope::ProfScope(const char *name, cudaStream_t stream)
 
 ProfScope::~ProfScope()
 {
+    nvtxRangePop();
     if (begin_ == nullptr)
         return;
     cudaEvent_t end = take_event();
