@@ -78,7 +78,8 @@ typedef enum gee_status {
     GEE_ERR_OOM = 5,          /* device memory exhausted */
     GEE_ERR_CUDA = 6,         /* a CUDA runtime call failed */
     GEE_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
-    GEE_ERR_UNSUPPORTED = 8   /* e.g. K > GEE_MAX_CLASSES */
+    GEE_ERR_UNSUPPORTED = 8,  /* e.g. K > GEE_MAX_CLASSES */
+    GEE_ERR_CANCELLED = 9     /* a server request cancelled before it ran */
 } gee_status;
 
 /* Edge-pass strategy of the edge-list entry points.  AUTO takes the choice
@@ -404,6 +405,11 @@ GEE_API gee_status gee_server_submit(gee_server *srv, const gee_request *req,
  * waited for once. */
 GEE_API gee_status gee_server_wait(gee_server *srv, int64_t ticket,
                                    double *latency_ms);
+/* Cancels a request that is still waiting for admission: it is removed
+ * from the queue and finishes with GEE_ERR_CANCELLED (returned by its
+ * gee_server_wait, its Z_h untouched).  GEE_ERR_INVALID_ARG for an unknown
+ * ticket or one already running or done (it then completes as usual). */
+GEE_API gee_status gee_server_cancel(gee_server *srv, int64_t ticket);
 GEE_API gee_status gee_server_get_stats(gee_server *srv,
                                         gee_server_stats *out);
 /* Finishes every queued request, then releases the server and its graphs.
@@ -452,6 +458,13 @@ typedef struct gee_kernel_time {
 
 GEE_API void gee_profile_enable(int32_t on);
 GEE_API int32_t gee_profile_read(gee_kernel_time *out, int32_t max_entries);
+
+/* Fault injection for tests: the next `count` device allocations made by
+ * the library (scratch of a call, arrays of a resident graph) fail as if the
+ * device were out of memory, so the calls that make them return GEE_ERR_OOM
+ * and release what they had taken; 0 clears it.  The failure is made on the
+ * host -- no allocation is attempted -- and the library stays usable. */
+GEE_API void gee_debug_fail_allocs(int32_t count);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ from ._lib import (GeeError, HUB_DEGREE, MAX_CLASSES, NOALLOC_MAX_NODES, STATUS,
                    STRATEGIES, STRATEGY_NAMES, KernelTime, check, lib, options)
 
 __all__ = ["GeeError", "Graph", "embed", "embed_host", "histogram",
-           "pick_strategy", "workspace_bytes", "status_string", "STATUS",
+           "pick_strategy", "workspace_bytes", "debug_fail_allocs", "status_string", "STATUS",
            "STRATEGIES", "MAX_CLASSES", "HUB_DEGREE", "load", "profile_enable",
            "profile_read", "embed_noalloc", "NOALLOC_MAX_NODES", "embed_batch",
            "Server", "autotune", "tune_table", "tune_set"]
@@ -94,6 +94,12 @@ def histogram(Y, K: int, stream=None):
                              ctypes.c_void_p(counts.data_ptr()), _stream_handle(stream))
     check(rc, "gee_histogram")
     return counts
+
+
+def debug_fail_allocs(count: int) -> None:
+    """Test hook (gee_debug_fail_allocs): the next ``count`` device
+    allocations of the library fail as if the device were out of memory."""
+    lib().gee_debug_fail_allocs(int(count))
 
 
 def pick_strategy(s: int, n: int, K: int, strategy="auto", private_max_cells=0) -> str:
@@ -471,6 +477,13 @@ class Server:
             check(rc, "gee_server_wait")
             return out, lat.value
         return out, lat.value, STATUS_NAMES.get(rc, str(rc))
+
+    def cancel(self, ticket: int) -> bool:
+        """gee_server_cancel: True if the request was still waiting and is
+        now cancelled (its wait then reports GEE_ERR_CANCELLED), False if it
+        is already running or done."""
+        rc = lib().gee_server_cancel(self.handle, int(ticket))
+        return rc == STATUS["GEE_OK"]
 
     def stats(self) -> dict:
         st = _lib_mod.ServerStats()

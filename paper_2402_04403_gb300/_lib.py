@@ -20,6 +20,7 @@ STATUS_NAMES = {
     6: "GEE_ERR_CUDA",
     7: "GEE_ERR_TIMEOUT",
     8: "GEE_ERR_UNSUPPORTED",
+    9: "GEE_ERR_CANCELLED",
 }
 STATUS = {v: k for k, v in STATUS_NAMES.items()}
 STRATEGIES = {"auto": 0, "atomic": 1, "private": 2, "segmented": 3}
@@ -153,6 +154,8 @@ SIGNATURES = {
     "gee_server_drop_graph": (ctypes.c_int, [_P, _I64]),
     "gee_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]),
     "gee_server_wait": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_double)]),
+    "gee_server_cancel": (ctypes.c_int, [_P, _I64]),
+    "gee_debug_fail_allocs": (None, [_I32]),
     "gee_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "gee_server_destroy": (None, [_P]),
     "gee_profile_enable": (None, [_I32]),

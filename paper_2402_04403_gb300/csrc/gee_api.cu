@@ -1,6 +1,7 @@
 // gee_api.cu -- the C ABI of libgee (declared in include/gee.h): argument
 // checks, scratch memory, strategy choice, launch sequence and status
 // read-back.  Every kernel lives in gee_coo.cu or gee_csr.cu.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -14,6 +15,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int g_sms[kMaxDevices];
 int g_smem[kMaxDevices];
+std::atomic<int32_t> g_fail_allocs{0};
 cudaMemPool_t g_pool[kMaxDevices];
 bool g_pool_ready[kMaxDevices];
 
@@ -86,6 +88,8 @@ class GraphAllocator : public Allocator {
     explicit GraphAllocator(std::vector<void *> *owned) : owned_(owned) {}
     cudaError_t alloc(void **p, size_t bytes) override
     {
+        if (injected_alloc_failure())
+            return cudaErrorMemoryAllocation;
         if (bytes == 0)
             bytes = 16;
         bytes = (bytes + 255) & ~size_t(255);
@@ -477,6 +481,15 @@ int sm_count()
     return g_sms[dev];
 }
 
+bool injected_alloc_failure()
+{
+    int32_t left = g_fail_allocs.load(std::memory_order_relaxed);
+    while (left > 0)
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1))
+            return true;
+    return false;
+}
+
 int max_block_smem()
 {
     int dev = 0;
@@ -645,6 +658,11 @@ gee_status embed_graph_dev(Workspace &ws, gee_graph *graph, const int32_t *Y,
 
 extern "C" {
 
+void gee_debug_fail_allocs(int32_t count)
+{
+    gee::g_fail_allocs.store(count > 0 ? count : 0);
+}
+
 void gee_options_default(gee_options *opts)
 {
     if (opts == nullptr)
@@ -668,6 +686,7 @@ const char *gee_status_string(gee_status status)
     case GEE_ERR_CUDA: return "CUDA runtime error";
     case GEE_ERR_TIMEOUT: return "device wait timed out";
     case GEE_ERR_UNSUPPORTED: return "unsupported argument";
+    case GEE_ERR_CANCELLED: return "request cancelled";
     }
     return "unknown status";
 }

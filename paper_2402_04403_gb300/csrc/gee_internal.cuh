@@ -113,6 +113,10 @@ int sm_count();
 // Dynamic shared memory one CTA may opt into on the current device.
 int max_block_smem();
 
+// True when gee_debug_fail_allocs asks the next allocation to fail (the
+// request is consumed).
+bool injected_alloc_failure();
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `stream` and return cudaGetLastError().
 
@@ -239,6 +243,8 @@ class Workspace : public Allocator {
     Workspace &operator=(const Workspace &) = delete;
     cudaError_t alloc(void **p, size_t bytes) override
     {
+        if (injected_alloc_failure())
+            return cudaErrorMemoryAllocation;
         if (!pool_) {
             cudaError_t e = device_pool(&pool_);
             if (e != cudaSuccess)

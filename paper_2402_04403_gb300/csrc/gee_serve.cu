@@ -764,6 +764,24 @@ gee_status gee_server_wait(gee_server *srv, int64_t ticket, double *latency_ms)
     return st;
 }
 
+gee_status gee_server_cancel(gee_server *srv, int64_t ticket)
+{
+    if (srv == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end())
+        return GEE_ERR_INVALID_ARG;
+    for (auto p = srv->pending.begin(); p != srv->pending.end(); ++p)
+        if (*p == it->second) {
+            srv->pending.erase(p);
+            srv->finish(it->second, GEE_ERR_CANCELLED);
+            srv->cv_done.notify_all();
+            return GEE_OK;
+        }
+    return GEE_ERR_INVALID_ARG;  // admitted or done
+}
+
 gee_status gee_server_get_stats(gee_server *srv, gee_server_stats *out)
 {
     if (srv == nullptr || out == nullptr)

@@ -67,6 +67,13 @@ def test_default_options(gee):
             o.deterministic) == (0, 1, 0, 0, 0)
 
 
+def test_fault_hook_and_cancel_need_no_gpu(gee):
+    lib = gee.load()
+    assert gee.status_string(9) == "request cancelled"
+    assert lib.gee_server_cancel(ctypes.c_void_p(), 1) == 1  # no server
+    lib.gee_debug_fail_allocs(0)
+
+
 def test_deterministic_refusals_need_no_gpu(gee):
     """Deterministic float sums need the pull form: the scatter strategies
     and weighted batch problems are refused on the host (GEE_ERR_UNSUPPORTED
