@@ -67,6 +67,13 @@ def test_default_options(gee):
             o.deterministic) == (0, 1, 0, 0, 0)
 
 
+def test_python_options_reach_the_struct(gee):
+    o = gee._lib.options("segmented", validate_edges=False, private_max_cells=7,
+                         block=64, deterministic=True)
+    assert (o.strategy, o.validate_edges, o.private_max_cells, o.block,
+            o.deterministic) == (gee.STRATEGIES["segmented"], 0, 7, 64, 1)
+
+
 def test_fault_hook_and_cancel_need_no_gpu(gee):
     lib = gee.load()
     assert gee.status_string(9) == "request cancelled"
