@@ -85,6 +85,30 @@ def test_exhaustive_three_node_graphs():
                     assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
 
 
+def test_exhaustive_four_node_graphs():
+    """Every edge set on 4 nodes (10 pairs, self-loops included) under
+    every labelling with classes {-1, 0, 1}, random orientations: counts and
+    FP64 values against exact rationals computed pair by pair."""
+    pairs = [(u, v) for u in range(4) for v in range(u, 4)]
+    labellings = list(itertools.product([-1, 0, 1], repeat=4))
+    rng = np.random.default_rng(1)
+    for mask in range(1 << len(pairs)):
+        chosen = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        edges = [(v, u) if rng.random() < 0.5 else (u, v) for u, v in chosen]
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        for Yt in labellings:
+            Y = np.asarray(Yt, dtype=np.int32)
+            C = oracle.counts(e, Y, 2)
+            Z = oracle.embed(e, Y, 2)
+            exact = _pins.pairwise_exact(edges, list(Yt), 2)
+            nk = [Yt.count(0), Yt.count(1)]
+            for u in range(4):
+                for k in range(2):
+                    q = exact[u][k]
+                    assert Fraction(int(C[u, k]), nk[k] or 1) == q, (mask, Yt, u, k)
+                    assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_row_and_column_sum_invariants(seed):
     n, s, K = 300, 2000, 6
