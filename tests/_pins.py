@@ -89,6 +89,55 @@ def pairwise_exact(edges, Y, K):
     return Z
 
 
+def pairwise_exact_weighted(edges, w, Y, K):
+    """Exact rational Z for dyadic edge weights (each w exactly a float32 of
+    few bits) by summing over node pairs: A[u, v] = sum of the weights of the
+    listed edges {u, v}, counted in both directions, then
+    Z[u, k] = sum_v A[u, v] [Y[v] = k] / n_k."""
+    n = len(Y)
+    A = [[Fraction(0)] * n for _ in range(n)]
+    for (u, v), x in zip(edges, w):
+        q = Fraction(float(x))
+        A[u][v] += q
+        A[v][u] += q
+    nk = [sum(1 for y in Y if y == k) for k in range(K)]
+    Z = [[Fraction(0)] * K for _ in range(n)]
+    for u in range(n):
+        for v in range(n):
+            if A[u][v] != 0 and Y[v] >= 0:
+                Z[u][Y[v]] += A[u][v] / nk[Y[v]]
+    return Z
+
+
+def pairwise_laplacian_decimal(edges, w, Y, K, digits=40):
+    """Z of the normalised adjacency D^-1/2 A D^-1/2 with non-negative
+    weights, node pair by node pair, in `digits`-digit decimal arithmetic:
+    A and the weighted degrees d_u = sum_v A[u, v] exactly as rationals, then
+    Z[u, k] = sum_v A[u, v] / sqrt(d_u d_v) [Y[v] = k] / n_k."""
+    import decimal
+    ctx = decimal.Context(prec=digits)
+    n = len(Y)
+    A = [[Fraction(0)] * n for _ in range(n)]
+    for (u, v), x in zip(edges, w):
+        q = Fraction(float(x))
+        A[u][v] += q
+        A[v][u] += q
+    d = [sum(row) for row in A]
+    nk = [sum(1 for y in Y if y == k) for k in range(K)]
+
+    def dec(q: Fraction):
+        return ctx.divide(decimal.Decimal(q.numerator), decimal.Decimal(q.denominator))
+
+    Z = [[decimal.Decimal(0)] * K for _ in range(n)]
+    for u in range(n):
+        for v in range(n):
+            if A[u][v] != 0 and Y[v] >= 0:
+                root = ctx.sqrt(dec(d[u] * d[v]))
+                term = ctx.divide(dec(A[u][v] / nk[Y[v]]), root)
+                Z[u][Y[v]] = ctx.add(Z[u][Y[v]], term)
+    return Z
+
+
 def round_fraction_to_f32(q: Fraction) -> np.float32:
     """Correctly rounded (nearest, ties to even) float32 of a non-negative
     rational, computed with exact integer arithmetic (normal range only)."""

@@ -109,6 +109,64 @@ def test_exhaustive_four_node_graphs():
                     assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
 
 
+def _four_node_edge_sets(seed):
+    """Every edge set on 4 nodes (10 pairs, self-loops included), each edge
+    in a random orientation."""
+    pairs = [(u, v) for u in range(4) for v in range(u, 4)]
+    rng = np.random.default_rng(seed)
+    for mask in range(1 << len(pairs)):
+        chosen = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        yield mask, [(v, u) if rng.random() < 0.5 else (u, v) for u, v in chosen]
+
+
+def test_exhaustive_four_node_graphs_signed_dyadic_weights():
+    """Every edge set on 4 nodes with signed weights in steps of 1/8 (a
+    repeated pair sums its weights; cancellation to zero happens), under
+    sampled labellings with classes {-1, 0, 1, 2}: FP64 values against exact
+    rationals computed pair by pair."""
+    rng = np.random.default_rng(2)
+    labellings = list(itertools.product([-1, 0, 1, 2], repeat=4))
+    for mask, edges in _four_node_edge_sets(3):
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        w = (rng.integers(-16, 17, size=len(edges)) / 8.0).astype(np.float32)
+        if len(edges) > 1 and rng.random() < 0.25:
+            # a listed duplicate whose weight cancels its twin
+            e = np.vstack([e, e[:1, ::-1]])
+            w = np.concatenate([w, -w[:1]])
+        for li in rng.choice(len(labellings), size=4, replace=False):
+            Yt = labellings[li]
+            Y = np.asarray(Yt, dtype=np.int32)
+            Z = oracle.embed(e, Y, 3, weights=w)
+            exact = _pins.pairwise_exact_weighted(e.tolist(), w, list(Yt), 3)
+            for u in range(4):
+                for k in range(3):
+                    q = exact[u][k]
+                    assert abs(Z[u, k] - float(q)) <= 1e-14 * max(1.0, abs(float(q))), \
+                        (mask, Yt, u, k, Z[u, k], q)
+
+
+def test_exhaustive_four_node_graphs_laplacian():
+    """Every edge set on 4 nodes with non-negative weights in steps of 1/8
+    (zero weights included, so some listed edges leave a degree at zero),
+    Laplacian form, under sampled labellings: FP64 values against a 40-digit
+    decimal evaluation of D^-1/2 A D^-1/2 W pair by pair."""
+    rng = np.random.default_rng(4)
+    labellings = list(itertools.product([-1, 0, 1], repeat=4))
+    for mask, edges in _four_node_edge_sets(5):
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        w = (rng.integers(0, 17, size=len(edges)) / 8.0).astype(np.float32)
+        for li in rng.choice(len(labellings), size=3, replace=False):
+            Yt = labellings[li]
+            Y = np.asarray(Yt, dtype=np.int32)
+            Z = oracle.embed(e, Y, 2, weights=w, laplacian=True)
+            ref = _pins.pairwise_laplacian_decimal(e.tolist(), w, list(Yt), 2)
+            for u in range(4):
+                for k in range(2):
+                    q = float(ref[u][k])
+                    assert abs(Z[u, k] - q) <= 1e-14 * max(1.0, abs(q)), \
+                        (mask, Yt, u, k, Z[u, k], q)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_row_and_column_sum_invariants(seed):
     n, s, K = 300, 2000, 6
