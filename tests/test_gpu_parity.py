@@ -125,7 +125,8 @@ def test_random_multigraphs(gee, n, s, K, frac, weighted):
 
 @pytest.fixture(scope="module")
 def rmat16():
-    """R-MAT scale 16, 2^20 edges: hubs far above the 4096-arc hub threshold."""
+    """R-MAT scale 16, 2^20 edges: hub rows of many 2,048-arc chunks (the
+    largest has more than 16,384 arcs)."""
     n = 1 << 16
     edges = graphgen.rmat_edges(16, n, 0, 1 << 20, seed=21)
     deg = np.bincount(edges.ravel(), minlength=n)
