@@ -154,7 +154,8 @@ GEE_API gee_status gee_embed(const int32_t *edges, const float *weights, int64_t
                      float *Z, const gee_options *opts, gee_stream_t stream);
 
 /* Same as gee_embed with host buffers: copies edges/weights/Y to the device,
- * runs the pass and copies Z back to Z_h (pinned host memory is fastest). */
+ * runs the pass and copies Z back to Z_h (pinned host memory is fastest).
+ * Same errors as gee_embed; Z_h is untouched unless the call succeeds. */
 GEE_API gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
                           int64_t s, const int32_t *Y_h, int64_t n, int32_t K,
                           int32_t laplacian, float *Z_h,
@@ -167,8 +168,13 @@ GEE_API gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h
  * into chunks).  This is the layout the paper's Ligra version iterates
  * (Section III: edgeMapDense walks each node's edge list); repeated
  * embeddings of the same graph with new label vectors then skip the upload
- * and the sort.  Validates endpoints (GEE_ERR_NODE_RANGE, no graph).
- * edges/weights are device pointers and are not referenced after return.
+ * and the sort.  edges/weights are device pointers and are not referenced
+ * after return; the graph owns its device arrays until gee_graph_destroy.
+ * Negative weights are accepted (a Laplacian pass on such a graph fails).
+ * Errors, with *out set to NULL: GEE_ERR_INVALID_ARG (out NULL, edges NULL
+ * with s > 0, misaligned edges or weights, negative s or n),
+ * GEE_ERR_OVERFLOW (n >= 2^31), GEE_ERR_NODE_RANGE (an endpoint outside
+ * [0, n)), GEE_ERR_OOM.
  */
 #define GEE_HUB_DEGREE 128
 typedef struct gee_graph gee_graph;
@@ -179,9 +185,13 @@ GEE_API gee_status gee_graph_create(const int32_t *edges, const float *weights,
 
 /* Z = A W for a resident graph and a label vector: Y device int32 [n],
  * Z device float [n][K] written in full, n the graph's.  Unit-weight
- * graphs give the bit-exact counts result.  opts is accepted for symmetry
- * (the resident pass has no strategy choice).  Calls on different streams
- * may use one graph at the same time. */
+ * graphs give the bit-exact counts result.  opts may be NULL; of it only
+ * deterministic is read (the resident pass has no strategy choice; block,
+ * if set, must still be valid).  Calls on different streams may use one
+ * graph at the same time.  Errors: GEE_ERR_INVALID_ARG (graph, Y or Z NULL,
+ * Y or Z misaligned, Laplacian on a graph with a negative weight),
+ * GEE_ERR_UNSUPPORTED (K > GEE_MAX_CLASSES), GEE_ERR_LABEL_RANGE with Z
+ * untouched, GEE_ERR_OOM when the scratch does not fit. */
 GEE_API gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
                            int32_t laplacian, float *Z,
                            const gee_options *opts, gee_stream_t stream);
@@ -194,6 +204,9 @@ GEE_API gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K
  * float [n][L*K] row-major, Z[u][l*K + k] = the embedding of node u for
  * label vector l.  Each vector has its own class sizes.  L >= 1, L*K <=
  * GEE_MAX_COLUMNS.  Same results as L separate gee_embed_graph calls.
+ * Errors as gee_embed_graph, plus GEE_ERR_INVALID_ARG for L < 1 and
+ * GEE_ERR_UNSUPPORTED for L*K > GEE_MAX_COLUMNS; a bad label in any vector
+ * fails the whole call with Z untouched.
  */
 GEE_API gee_status gee_embed_graph_multi(gee_graph *graph, const int32_t *Y,
                                          int32_t L, int32_t K,
