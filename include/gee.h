@@ -415,7 +415,8 @@ GEE_API gee_status gee_server_submit(gee_server *srv, const gee_request *req,
                                      int64_t *ticket);
 /* Blocks until the request is done; returns its status and, if latency_ms
  * is not NULL, the time from submission to completion.  Each ticket can be
- * waited for once. */
+ * waited for once: a second wait, also one from another thread while the
+ * first is still blocked, returns GEE_ERR_INVALID_ARG. */
 GEE_API gee_status gee_server_wait(gee_server *srv, int64_t ticket,
                                    double *latency_ms);
 /* Cancels a request that is still waiting for admission: it is removed

@@ -50,6 +50,7 @@ struct Req {
     Clock::time_point t0, t1;
     gee_status status = GEE_OK;
     bool done = false;
+    bool waited = false;       // a gee_server_wait has claimed it
 };
 
 struct GraphEntry {
@@ -754,6 +755,9 @@ gee_status gee_server_wait(gee_server *srv, int64_t ticket, double *latency_ms)
     if (it == srv->reqs.end())
         return GEE_ERR_INVALID_ARG;
     Req *q = it->second;
+    if (q->waited)
+        return GEE_ERR_INVALID_ARG;  // another thread waits for it already
+    q->waited = true;
     srv->cv_done.wait(lk, [q] { return q->done; });
     const gee_status st = q->status;
     if (latency_ms != nullptr)
