@@ -262,15 +262,19 @@ def cpu_baseline(w, use_gpu, shift=5):
             "seconds": secs}
 
 
+# seconds of oracle work one `--impl reference` run aims at
+REFERENCE_SECONDS = 120.0
+
+
 def run_reference(args, w, world, rank):
     if rank != 0:
         return
     import torch
     use_gpu = torch.cuda.is_available()
-    # size each step's sample so the whole run stays near two minutes
+    # size each step's sample so the whole run stays near REFERENCE_SECONDS
     probe = sample_inputs(w, 12, use_gpu)
     rate = probe["s"] / max(time_oracle(probe, w), 1e-4)
-    per_step = 120.0 / max(1, args.steps + args.warmup)
+    per_step = REFERENCE_SECONDS / max(1, args.steps + args.warmup)
     shift = 12
     while shift > 4 and (w["s"] >> (shift - 1)) / rate < per_step:
         shift -= 1

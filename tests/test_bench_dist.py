@@ -54,3 +54,36 @@ def test_algorithmic_bytes_of_the_paper_workload():
     w = bench.WORKLOADS["paper"]
     assert bench.algorithmic_bytes(w) == 27_782_400_000
     assert bench.pull_bytes(w) == 27_585_600_000
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """`bench.py --impl reference` on the host cores: one JSON line with the
+    keys of the benchmark contract (sample kept tiny here)."""
+    import argparse
+    import json
+    import bench
+    monkeypatch.setattr(bench, "REFERENCE_SECONDS", 1e-3)
+    args = argparse.Namespace(steps=2, warmup=1, gpus=1, workload="paper")
+    bench.run_reference(args, bench.WORKLOADS["paper"], 1, 0)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "edges/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 1)
+    assert line["ms_per_step"] > 0 and line["data"] == "synthetic"
+    assert line["config"]["name"] == "paper" and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "R-MAT scale 14" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "edges/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_is_silent_on_other_ranks(capsys):
+    import argparse
+    import bench
+    args = argparse.Namespace(steps=1, warmup=0, gpus=2, workload="paper")
+    bench.run_reference(args, bench.WORKLOADS["paper"], 2, 1)
+    assert capsys.readouterr().out == ""
