@@ -42,6 +42,8 @@ TAG_SHUFFLE = 0x53484646  # "SHFF"
 TAG_PLANTED = 0x504C4E54  # "PLNT"
 
 RMAT_MAX_ATTEMPTS = 64
+# elements per host batch: keeps the Philox temporaries cache-sized
+_HOST_CHUNK = 1 << 14
 # odd multipliers of the id bijection (any odd constants work)
 _PERM_MUL1 = 0x2545F491
 _PERM_MUL2 = 0x9E3779B1
@@ -128,11 +130,26 @@ def _rmat_attempt(idx, attempt, scale, thr, seed):
     return permute_ids(u, scale, seed), permute_ids(v, scale, seed)
 
 
+def _in_chunks(fn, start, count, out):
+    """Fill out[0:count] with fn(start + i, m) over consecutive batches of
+    at most _HOST_CHUNK elements (every element is a pure function of its
+    index, so the batching does not change any value)."""
+    for i in range(0, count, _HOST_CHUNK):
+        m = min(_HOST_CHUNK, count - i)
+        out[i:i + m] = fn(start + i, m)
+    return out
+
+
 def rmat_edges(scale, n, start, count, seed, a=0.57, b=0.19, c=0.19):
     """Edges [start, start+count) of the seeded R-MAT graph, (count, 2) int32."""
     if n > (1 << scale) or n < 1:
         raise ValueError("need 1 <= n <= 2^scale")
     thr = rmat_thresholds(a, b, c)
+    return _in_chunks(lambda st, m: _rmat_block(scale, n, st, m, seed, thr),
+                      start, count, np.empty((count, 2), np.int32))
+
+
+def _rmat_block(scale, n, start, count, seed, thr):
     idx = np.arange(start, start + count, dtype=np.uint64)
     out_u = np.zeros(count, np.uint64)
     out_v = np.zeros(count, np.uint64)
@@ -162,6 +179,11 @@ def unlabeled_threshold(frac_unlabeled):
 
 def labels(n, K, seed, frac_unlabeled=0.0, start=0):
     """Y[i] uniform in [0, K), or -1 with probability frac_unlabeled."""
+    return _in_chunks(lambda st, m: _labels_block(m, K, seed, frac_unlabeled, st),
+                      start, n, np.empty(n, np.int32))
+
+
+def _labels_block(n, K, seed, frac_unlabeled, start):
     idx = np.arange(start, start + n, dtype=np.uint64)
     w = _words(idx, 0, TAG_LABEL, seed)
     cls = ((w[1].astype(np.uint64) * np.uint64(K)) >> np.uint64(32)).astype(np.int32)
@@ -173,6 +195,11 @@ def labels(n, K, seed, frac_unlabeled=0.0, start=0):
 
 def weights(s, seed, start=0):
     """w[i] = (top 24 bits + 1) / 2^24, uniform on (0, 1], exact in float32."""
+    return _in_chunks(lambda st, m: _weights_block(m, seed, st),
+                      start, s, np.empty(s, np.float32))
+
+
+def _weights_block(s, seed, start):
     idx = np.arange(start, start + s, dtype=np.uint64)
     w = _words(idx, 0, TAG_WEIGHT, seed)
     return (((w[0] >> np.uint32(8)).astype(np.float64) + 1.0) / 16777216.0
