@@ -109,6 +109,32 @@ def test_exhaustive_four_node_graphs():
                     assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
 
 
+def test_exhaustive_five_node_edge_sets():
+    """Every edge set on 5 nodes (15 pairs, self-loops included; 32,768
+    graphs), random orientations, each under two labellings drawn from
+    {-1, 0, 1}^5: exact counts and FP64 values against exact rationals
+    computed pair by pair."""
+    pairs = [(u, v) for u in range(5) for v in range(u, 5)]
+    labellings = list(itertools.product([-1, 0, 1], repeat=5))
+    rng = np.random.default_rng(6)
+    for mask in range(1 << len(pairs)):
+        chosen = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        edges = [(v, u) if rng.random() < 0.5 else (u, v) for u, v in chosen]
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        for li in rng.integers(0, len(labellings), size=2):
+            Yt = labellings[li]
+            Y = np.asarray(Yt, dtype=np.int32)
+            C = oracle.counts(e, Y, 2)
+            Z = oracle.embed(e, Y, 2)
+            exact = _pins.pairwise_exact(edges, list(Yt), 2)
+            nk = [Yt.count(0) or 1, Yt.count(1) or 1]
+            for u in range(5):
+                for k in range(2):
+                    q = exact[u][k]
+                    assert Fraction(int(C[u, k]), nk[k]) == q, (mask, Yt, u, k)
+                    assert abs(Z[u, k] - float(q)) <= 1e-15 * max(1.0, float(q))
+
+
 def _four_node_edge_sets(seed):
     """Every edge set on 4 nodes (10 pairs, self-loops included), each edge
     in a random orientation."""
