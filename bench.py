@@ -252,10 +252,28 @@ def time_oracle(sample, w):
     return time.perf_counter() - t
 
 
+def host_cpu():
+    """The host the oracle is timed on: logical CPUs and the CPU model (x86
+    'model name', else the Arm implementer/part codes of /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            fields = dict(l.split(":", 1) for l in fh.read().splitlines() if ":" in l)
+        fields = {k.strip(): v.strip() for k, v in fields.items()}
+        model = fields.get("model name") or (
+            f"implementer {fields['CPU implementer']} part {fields['CPU part']}"
+            if "CPU part" in fields else None)
+    except (OSError, KeyError, ValueError):
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def cpu_baseline(w, use_gpu, shift=5):
     smp = sample_inputs(w, shift, use_gpu)
     secs = time_oracle(smp, w)
     return {"value": smp["s"] / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": (f"R-MAT scale {smp['scale']}: n={smp['n']}, s={smp['s']} "
                        f"(1/{1 << shift} of the workload, same generator and label mix), "
                        f"serial C FP64 oracle, {secs:.2f} s"),
@@ -293,7 +311,7 @@ def run_reference(args, w, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_for(args, w),
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

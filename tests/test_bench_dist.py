@@ -77,6 +77,7 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert "R-MAT scale 14" in cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["machine"]
     assert line["e2e"] == {"value": line["value"], "unit": "edges/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
