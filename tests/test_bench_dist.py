@@ -88,3 +88,24 @@ def test_reference_arm_is_silent_on_other_ranks(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2, workload="paper")
     bench.run_reference(args, bench.WORKLOADS["paper"], 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_ncu_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The committed DRAM figure is reported only while the profile's source
+    digest matches the current edge-pass sources; after any change to them
+    the bench reports null."""
+    import bench
+    csrc = tmp_path / "paper_2402_04403_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "gee_csr.cu").write_text("kernel v1\n")
+    (csrc / "gee_internal.cuh").write_text("header\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    digest = bench.source_digest()
+    (tmp_path / "profiles" / "k_pull_paper.md").write_text(
+        f"source_digest: {digest}\ntraffic_bytes_per_launch: 2.862e10\n")
+    assert bench.ncu_traffic("k_pull", "paper") == 2.862e10
+    assert bench.ncu_traffic("k_pull", "rmat24") is None      # no summary
+    (csrc / "gee_csr.cu").write_text("kernel v2\n")
+    assert bench.source_digest() != digest
+    assert bench.ncu_traffic("k_pull", "paper") is None
