@@ -2,7 +2,7 @@
 "Edge-Parallel Graph Encoder Embedding", arXiv 2402.04403).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
-benchmark's CPU-baseline leg are the only callers.  The GPU library never
+benchmark's CPU-baseline leg and reference arm are the only callers.  The GPU library never
 imports this package and this package never imports the GPU library; they
 share no code.
 

@@ -29,11 +29,14 @@
  * same edge loop runs.  A node with d = 0 contributes nothing.
  *
  * Pins (tests under -m "not gpu"): hand-worked cases in tests/golden, the
- * dense closed form (M + M^T) W, exhaustive enumeration of all graphs on
- * three nodes, row/column-sum invariants, equivariance under edge shuffles and
- * node/class permutations, the K = 1 degree special case, SBM block means, and
- * scipy's normalised Laplacian for the Laplacian reading.  The paper prints no
- * embedding values, so nothing here is pinned to a printed number.
+ * dense closed form (M + M^T) W, exhaustive enumeration of all edge sets on
+ * three, four and five nodes against exact rationals (on four nodes also
+ * with signed dyadic weights, and in Laplacian form against a 40-digit
+ * decimal evaluation), row/column-sum invariants, equivariance under edge
+ * shuffles and node/class permutations, the K = 1 degree special case, SBM
+ * block means, and scipy's normalised Laplacian for the Laplacian reading.
+ * The paper prints no embedding values, so nothing here is pinned to a
+ * printed number.
  *
  * Build: cc -O2 -std=c99 -ffp-contract=off -shared -fPIC gee_oracle.c -lm
  * (-ffp-contract=off keeps every product and sum separately rounded, so x86
