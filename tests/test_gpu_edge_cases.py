@@ -64,6 +64,29 @@ def test_resident_single_and_multi(gee, name):
                                       oracle.embed_counts32(edges, Ys[l], K)), (K, l)
 
 
+def test_zero_nodes(gee):
+    """n = 0 (no nodes, no edges): every form succeeds with an empty Z, and
+    every class size is 0."""
+    import torch
+    e = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    Y = torch.zeros(0, dtype=torch.int32, device="cuda")
+    assert gee.histogram(Y, 4).cpu().tolist() == [0, 0, 0, 0]
+    for strategy in ("atomic", "private", "segmented"):
+        for lap in (False, True):
+            Z = gee.embed(e, Y, 3, laplacian=lap, strategy=strategy)
+            assert tuple(Z.shape) == (0, 3)
+    Zh = gee.embed_host(np.zeros((0, 2), np.int32), np.zeros(0, np.int32), 3)
+    assert Zh.shape == (0, 3)
+    with gee.Graph(e, 0) as g:
+        assert g.info()["n"] == 0
+        assert tuple(g.embed(Y, 3).shape) == (0, 3)
+        assert tuple(g.embed(Y, 3, laplacian=True).shape) == (0, 3)
+        Ys = torch.zeros((9, 0), dtype=torch.int32, device="cuda")
+        assert tuple(g.embed_multi(Ys, 3).shape) == (0, 27)
+        assert g.embed_host(np.zeros(0, np.int32), 3).shape == (0, 3)
+    torch.cuda.synchronize()
+
+
 def test_1024_columns_with_one_class(gee):
     """L = 1,024 label vectors of K = 1 (32 blocks of 32 lanes, odd K)."""
     edges, n = CASES["star, hub in 5 chunks"]
