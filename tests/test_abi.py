@@ -208,3 +208,28 @@ def test_tuning_table_drives_auto_without_a_gpu(gee):
         gee.tune_set([])
     assert gee.tune_table() == []
     assert gee.pick_strategy(2048, 256, 16) in ("atomic", "private")
+
+
+def test_missing_library_fails_loudly(gee, monkeypatch, tmp_path):
+    """No CPU fallback: without libgee.so every entry point raises."""
+    from paper_2402_04403_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libgee.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gee.load()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gee.status_string(0)
+
+
+def test_host_tensors_are_refused_not_computed(gee):
+    """CPU tensors are rejected before any work: the device entry points
+    never compute on the host."""
+    import torch
+    e = torch.zeros((3, 2), dtype=torch.int32)
+    Y = torch.zeros(4, dtype=torch.int32)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        gee.embed(e, Y, 2)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        gee.Graph(e, 4)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        gee.histogram(Y, 2)
