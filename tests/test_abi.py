@@ -233,3 +233,25 @@ def test_host_tensors_are_refused_not_computed(gee):
         gee.Graph(e, 4)
     with pytest.raises(TypeError, match="CUDA tensor"):
         gee.histogram(Y, 2)
+
+
+def test_product_and_oracle_share_no_code():
+    """The library never imports, includes or loads the oracle, and the
+    oracle never imports, includes or loads the library."""
+    pkg = os.path.join(ROOT, "paper_2402_04403_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                continue
+            text = open(os.path.join(dirpath, f)).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+            assert not re.search(r"#\s*include\s*[<\"][^>\"]*oracle", text), f
+            assert "gee_oracle" not in text and "libgee_oracle" not in text, f
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if not f.endswith((".py", ".c", ".h")):
+            continue
+        text = open(os.path.join(odir, f)).read()
+        assert "paper_2402_04403_gb300" not in text, f
+        assert not re.search(r"#\s*include\s*[<\"](gee\.h|gee_internal)", text), f
+        assert "libgee.so" not in text, f
