@@ -102,3 +102,17 @@ def test_planted_partition_structure():
     # same seed, sliced: identical edges
     assert np.array_equal(graphgen.planted_edges(n, K, 100, 10.0, seed=4, start=50),
                           e[50:150])
+
+
+def test_host_batching_does_not_change_values(monkeypatch):
+    """The host generators draw in batches; any batch size gives the same
+    edges, labels and weights (each value is a function of its index)."""
+    ref = (graphgen.rmat_edges(12, 3000, 5, 1000, seed=8),
+           graphgen.labels(1000, 7, seed=9, frac_unlabeled=0.3, start=11),
+           graphgen.weights(1000, seed=10, start=13))
+    monkeypatch.setattr(graphgen, "_HOST_CHUNK", 7)
+    got = (graphgen.rmat_edges(12, 3000, 5, 1000, seed=8),
+           graphgen.labels(1000, 7, seed=9, frac_unlabeled=0.3, start=11),
+           graphgen.weights(1000, seed=10, start=13))
+    for a, b in zip(ref, got):
+        assert a.dtype == b.dtype and np.array_equal(a, b)
