@@ -261,8 +261,13 @@ GEE_API size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K,
  * and S[k][j] the exact class sums of C, node i moves to the non-empty class
  * k with the smallest sum over j = 0..K-1 (in order, FP32, each operation
  * rounded on its own) of (Z[i][j] - RN32(S[k][j]/(m_k m_j)))^2, the lowest k
- * on ties, so every run takes the same decisions.  Counts must stay below
- * 2^23.
+ * on ties, so every run takes the same decisions.  The paper fixes no
+ * precision for this step; the FP32 distances differ from exact ones by at
+ * most (K + 4) 2^-24 sum_j (|Z[i][j]| + |c[k][j]|)^2, so only classes whose
+ * means are that close to equally near can be chosen differently from an
+ * exact computation.  The counts are recovered from Z as rint(Z m_j), exact
+ * below 2^23: a graph with a row of 2^23 or more arcs returns
+ * GEE_ERR_OVERFLOW before any round runs.
  * GEE_ERR_UNSUPPORTED for weighted graphs or K > 64.
  */
 GEE_API gee_status gee_unsupervised(gee_graph *graph, int32_t *Y, int32_t K,

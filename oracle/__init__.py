@@ -75,10 +75,11 @@ def _lib():
                                                   p, i64, p, p]
             lib.gee_oracle_set_mutation.argtypes = [ci]
             lib.gee_oracle_unsupervised.argtypes = [p, i64, i64, i32, i32, p, p, p]
+            lib.gee_oracle_unsup_round.argtypes = [p, i64, i64, i32, p, p, p, p]
             for f in (lib.gee_oracle_class_counts, lib.gee_oracle_degrees,
                       lib.gee_oracle_embed, lib.gee_oracle_counts,
                       lib.gee_oracle_round_counts, lib.gee_oracle_embed_rows,
-                      lib.gee_oracle_unsupervised):
+                      lib.gee_oracle_unsupervised, lib.gee_oracle_unsup_round):
                 f.restype = ci
             lib.gee_oracle_set_mutation.restype = None
             _LIB = lib
@@ -200,3 +201,19 @@ def unsupervised(edges, Y0, K: int, max_iter: int = 50):
     _check(_lib().gee_oracle_unsupervised(_ptr(e), e.shape[0], y.size, int(K), int(max_iter),
                                           _ptr(y), ctypes.byref(rounds), _ptr(changes)))
     return y, rounds.value, changes[:rounds.value].tolist()
+
+
+def unsup_round(edges, Y, K: int):
+    """One round of the unsupervised loop (gee_oracle_unsup_round) from
+    labels Y: returns (next labels, D, T) with D[i, k] the FP64 squared
+    distance of node i's embedding to class k's mean (0 for empty classes)
+    and T[i, k] = sum_j (|Z[i,j]| + |c[k,j]|)^2, the scale of the rounding
+    error a finite-precision evaluation of D[i, k] can carry."""
+    e = _edges(edges)
+    y = np.ascontiguousarray(Y, dtype=np.int32)
+    nxt = np.zeros(max(y.size, 1), dtype=np.int32)
+    D = np.zeros((y.size, K), dtype=np.float64)
+    T = np.zeros((y.size, K), dtype=np.float64)
+    _check(_lib().gee_oracle_unsup_round(_ptr(e), e.shape[0], y.size, int(K), _ptr(y),
+                                         _ptr(nxt), _ptr(D), _ptr(T)))
+    return nxt[:y.size], D, T

@@ -389,18 +389,108 @@ int gee_oracle_embed_rows(const int32_t *E, const float *w, int64_t s,
  * rounds ran.  Unit weights, every label known (0..K-1).  With
  *   C       integer counts of the current labels (Alg. 1, unit weights)
  *   m_k     class sizes
- *   Z[i,j]  = RN32(C[i,j] / m_j), the float embedding of the count path
+ *   Z[i,j]  = C[i,j] / m_j                         (FP64, one division)
  *   S[k,j]  = sum of C[i,j] over i of class k      (exact integers)
- *   c[k,j]  = RN32(S[k,j] / (m_k * m_j))           (quotient formed in FP64)
+ *   c[k,j]  = S[k,j] / (m_k * m_j)                 (FP64 product, one division)
  *   d(i,k)  = sum over j = 0..K-1, in that order, of (Z[i,j] - c[k,j])^2
- *             in FP32, each difference, square and sum rounded separately
+ *             in FP64
  * node i moves to the k with the smallest d(i,k) among classes with
- * m_k > 0, the lowest k on ties.  (The paper fixes no precision for the
- * clustering step; distances are taken in the precision of the embedding.)  The labels are updated in place in Y;
- * *rounds receives the number of rounds run (the last one changed nothing
- * unless max_iter ended the loop) and changes[r] (if not NULL, length
- * max_iter) the number of nodes round r moved.
+ * m_k > 0, the lowest k on ties.  The paper fixes no precision for the
+ * clustering step, so the oracle takes it in FP64, close to the exact
+ * rational distances (the tests pin it to them); a faster implementation
+ * may take different decisions only where two class means are nearly
+ * equally near, which gee_oracle_unsup_round's distances let a test bound.
+ * The labels are updated in place in Y; *rounds receives the number of
+ * rounds run (the last one changed nothing unless max_iter ended the loop)
+ * and changes[r] (if not NULL, length max_iter) the number of nodes round r
+ * moved.
  */
+
+/* One assignment step from labels Y (all in 0..K-1) with counts C[n][K]
+ * and class sizes m[K] already taken: next[i] = the chosen class,
+ * D[i*K + k] (if not NULL) = d(i,k) (0 for empty classes) and T[i*K + k]
+ * (if not NULL) = sum over j of (|Z[i,j]| + |c[k,j]|)^2, the scale of the
+ * rounding error a finite-precision d(i,k) can carry.  Returns the nodes
+ * moved. */
+static int64_t unsup_assign(const uint64_t *C, const int64_t *m,
+                            const int32_t *Y, int64_t n, int32_t K,
+                            uint64_t *S, double *cen, int32_t *next,
+                            double *D, double *T)
+{
+    memset(S, 0, sizeof(uint64_t) * (size_t)K * (size_t)K);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < K; ++j)
+            S[(int64_t)Y[i] * K + j] += C[i * K + j];
+    for (int32_t k = 0; k < K; ++k)
+        for (int32_t j = 0; j < K; ++j) {
+            double den = (gee_oracle_mutation == 9)
+                             ? (double)m[k]
+                             : (double)m[k] * (double)m[j];
+            cen[k * K + j] = den > 0.0 ? (double)S[k * K + j] / den : 0.0;
+        }
+    int64_t moved = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t best = -1;
+        double bd = 0.0;
+        for (int32_t k = 0; k < K; ++k) {
+            double d = 0.0, t = 0.0;
+            if (m[k] != 0) {
+                for (int32_t j = 0; j < K; ++j) {
+                    double z = m[j] > 0
+                                   ? (double)C[i * K + j] / (double)m[j]
+                                   : 0.0;
+                    double c = cen[k * K + j];
+                    double diff = z - c;
+                    d = d + diff * diff;
+                    double a = fabs(z) + fabs(c);
+                    t = t + a * a;
+                }
+                if (best < 0 || d < bd) {
+                    best = k;
+                    bd = d;
+                }
+            }
+            if (D != NULL)
+                D[i * K + k] = d;
+            if (T != NULL)
+                T[i * K + k] = t;
+        }
+        next[i] = best;
+        moved += (best != Y[i]);
+    }
+    return moved;
+}
+
+/* One round of the loop (embed Y, then one assignment step), with the
+ * per-node distances to every class mean: next[n], D[n][K], T[n][K] as in
+ * unsup_assign (D and T may be NULL).  Y is not modified. */
+int gee_oracle_unsup_round(const int32_t *E, int64_t s, int64_t n, int32_t K,
+                           const int32_t *Y, int32_t *next, double *D,
+                           double *T)
+{
+    if (next == NULL && n > 0)
+        return ORC_BAD_ARG;
+    int st = check_inputs(E, NULL, s, Y, n, K, 0);
+    if (st != ORC_OK)
+        return st;
+    for (int64_t i = 0; i < n; ++i)
+        if (Y[i] < 0)
+            return ORC_BAD_LABEL;
+    uint64_t *C = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1) * (size_t)K);
+    uint64_t *S = malloc(sizeof(uint64_t) * (size_t)K * (size_t)K);
+    double *cen = malloc(sizeof(double) * (size_t)K * (size_t)K);
+    int64_t *m = malloc(sizeof(int64_t) * (size_t)K);
+    if (!C || !S || !cen || !m) {
+        free(C); free(S); free(cen); free(m);
+        return ORC_NO_MEMORY;
+    }
+    gee_oracle_counts(E, s, Y, n, K, C);
+    gee_oracle_class_counts(Y, n, K, m);
+    unsup_assign(C, m, Y, n, K, S, cen, next, D, T);
+    free(C); free(S); free(cen); free(m);
+    return ORC_OK;
+}
+
 int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
                             int32_t max_iter, int32_t *Y, int32_t *rounds,
                             int64_t *changes)
@@ -416,7 +506,7 @@ int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
             return ORC_BAD_LABEL;
     uint64_t *C = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1) * (size_t)K);
     uint64_t *S = malloc(sizeof(uint64_t) * (size_t)K * (size_t)K);
-    float *cen = malloc(sizeof(float) * (size_t)K * (size_t)K);
+    double *cen = malloc(sizeof(double) * (size_t)K * (size_t)K);
     int64_t *m = malloc(sizeof(int64_t) * (size_t)K);
     int32_t *next = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     if (!C || !S || !cen || !m || !next) {
@@ -426,42 +516,7 @@ int gee_oracle_unsupervised(const int32_t *E, int64_t s, int64_t n, int32_t K,
     for (int32_t r = 0; r < max_iter; ++r) {
         gee_oracle_counts(E, s, Y, n, K, C);
         gee_oracle_class_counts(Y, n, K, m);
-        memset(S, 0, sizeof(uint64_t) * (size_t)K * (size_t)K);
-        for (int64_t i = 0; i < n; ++i)
-            for (int32_t j = 0; j < K; ++j)
-                S[(int64_t)Y[i] * K + j] += C[i * K + j];
-        for (int32_t k = 0; k < K; ++k)
-            for (int32_t j = 0; j < K; ++j) {
-                double den = (gee_oracle_mutation == 9)
-                                 ? (double)m[k]
-                                 : (double)m[k] * (double)m[j];
-                cen[k * K + j] =
-                    den > 0.0 ? (float)((double)S[k * K + j] / den) : 0.0f;
-            }
-        int64_t moved = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            int32_t best = -1;
-            float bd = 0.0f;
-            for (int32_t k = 0; k < K; ++k) {
-                if (m[k] == 0)
-                    continue;
-                float d = 0.0f;
-                for (int32_t j = 0; j < K; ++j) {
-                    float z = m[j] > 0
-                                  ? (float)((double)C[i * K + j] / (double)m[j])
-                                  : 0.0f;
-                    float diff = z - cen[k * K + j];
-                    float sq = diff * diff;
-                    d = d + sq;
-                }
-                if (best < 0 || d < bd) {
-                    best = k;
-                    bd = d;
-                }
-            }
-            next[i] = best;
-            moved += (best != Y[i]);
-        }
+        int64_t moved = unsup_assign(C, m, Y, n, K, S, cen, next, NULL, NULL);
         memcpy(Y, next, sizeof(int32_t) * (size_t)n);
         if (changes != NULL)
             changes[r] = moved;

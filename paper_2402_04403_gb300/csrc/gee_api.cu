@@ -593,6 +593,8 @@ gee_status tile_split(gee_graph *g, int32_t cols, bool host_z,
 
 bool gee::graph_weighted(const gee_graph *graph) { return graph->csr.weighted; }
 
+uint32_t gee::graph_max_degree(const gee_graph *graph) { return graph->csr.max_deg; }
+
 gee_status gee::graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                                    const int32_t *Y, int32_t L, int32_t K,
                                    int32_t laplacian, float *Z,

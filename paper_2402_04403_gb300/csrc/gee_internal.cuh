@@ -403,6 +403,8 @@ bool tuned_choice(int64_t s, int64_t n, int32_t K, gee_strategy *strategy,
 // deterministic: float sums in fixed point (bitwise reproducible); not for
 // L >= kWideMinLabels with weights (GEE_ERR_UNSUPPORTED).
 bool graph_weighted(const gee_graph *graph);
+// Arcs of the graph's longest row (a self-loop gives its row two arcs).
+uint32_t graph_max_degree(const gee_graph *graph);
 gee_status graph_pass_enqueue(Workspace &ws, gee_graph *graph,
                               const int32_t *Y, int32_t L, int32_t K,
                               int32_t laplacian, float *Z, DevStatus **st,

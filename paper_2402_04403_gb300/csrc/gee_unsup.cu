@@ -6,7 +6,9 @@
 // pass: every round embeds the current labels (S1-S5 on the resident
 // graph) and moves each node to the nearest class mean of that embedding,
 // until a round moves nothing.  The arithmetic is fixed so that every run
-// -- and the serial oracle -- takes the same decisions:
+// takes the same decisions (the paper fixes no precision for this step; an
+// exact evaluation can differ only on near-ties, by the FP32 bound the
+// header states):
 //   Z[i,j]  = RN32(C[i,j] / m_j), the pass's bit-exact count-path output
 //   C[i,j]  = the exact neighbour count, recovered from Z as rint(Z * m_j)
 //             in FP64 (exact while C < 2^23)
@@ -196,6 +198,10 @@ extern "C" gee_status gee_unsupervised(gee_graph *graph, int32_t *Y, int32_t K,
         return rc;
     if (graph_weighted(graph))
         return GEE_ERR_UNSUPPORTED;
+    // every count is at most its row's arcs; rint(Z * m_j) recovers counts
+    // below 2^23 exactly (|Z m_j - C| <= C 2^-24 < 1/2), larger ones not
+    if (graph_max_degree(graph) >= (1u << 23))
+        return GEE_ERR_OVERFLOW;
     if (n > 0 && (Y == nullptr || Z == nullptr))
         return GEE_ERR_INVALID_ARG;
     if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Z)) & 3) != 0)

@@ -121,13 +121,18 @@ def test_batch_and_server_with_degenerate_problems(gee):
 
 
 def test_unsupervised_on_degenerate_graphs(gee):
+    """No edges, self-loops only, one star hub: every round within the FP32
+    rounding slack of the FP64 oracle's round from the same labels (ties
+    abound here), Z the embedding of the labels returned."""
+    from tests.test_gpu_unsup import _check_choice
     for name in ("no edges", "self-loops only", "star, hub in 5 chunks"):
         edges, n = CASES[name]
         K = min(3, n)
-        Y0 = graphgen.labels(n, K, seed=11)
-        want_y, want_rounds, want_moved = oracle.unsupervised(edges, Y0, K, max_iter=10)
+        Y = graphgen.labels(n, K, seed=11)
         with gee.Graph(_dev(edges), n) as g:
-            y, Z, rounds, moved = g.unsupervised(_dev(Y0), K, max_iter=10)
-        assert (rounds, moved) == (want_rounds, want_moved), name
-        assert np.array_equal(y.cpu().numpy(), want_y), name
-        assert np.array_equal(Z.cpu().numpy(), oracle.embed_counts32(edges, want_y, K)), name
+            for _ in range(4):
+                y, Z, rounds, moved = g.unsupervised(_dev(Y), K, max_iter=1)
+                got = y.cpu().numpy()
+                _check_choice(edges, Y, K, got)
+                assert np.array_equal(Z.cpu().numpy(), oracle.embed_counts32(edges, got, K)), name
+                Y = got

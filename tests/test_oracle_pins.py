@@ -363,8 +363,9 @@ def test_error_codes():
 def _exact_round(edges, Y, K):
     """One round written out with exact rationals, independently of the
     oracle: integer counts by a loop over the edges, class means, squared
-    distances; returns the new labels and, per node, the gap between the
-    best and the second-best distance (0 for ties)."""
+    distances; returns the new labels, per node the gap between the best
+    and the second-best distance relative to the best (0 for ties), and the
+    exact distances d[i][k] (None for empty classes)."""
     n = len(Y)
     C = [[0] * K for _ in range(n)]
     for u, v in edges:
@@ -375,33 +376,45 @@ def _exact_round(edges, Y, K):
          for i in range(n)]
     cen = [[Fraction(sum(C[i][j] for i in range(n) if Y[i] == k), m[k] * m[j])
             if m[k] and m[j] else Fraction(0) for j in range(K)] for k in range(K)]
-    new, gaps = [], []
+    new, gaps, dist = [], [], []
     for i in range(n):
-        d = sorted((sum((Z[i][j] - cen[k][j]) ** 2 for j in range(K)), k)
-                   for k in range(K) if m[k])
+        row = [sum((Z[i][j] - cen[k][j]) ** 2 for j in range(K)) if m[k] else None
+               for k in range(K)]
+        d = sorted((row[k], k) for k in range(K) if m[k])
         new.append(d[0][1])
         gaps.append((d[1][0] - d[0][0]) / (d[0][0] + Fraction(1, 10**6))
                     if len(d) > 1 else Fraction(1))
-    return new, gaps
+        dist.append(row)
+    return new, gaps, dist
 
 
 @pytest.mark.parametrize("seed", range(6))
 def test_unsupervised_round_matches_exact_rationals(seed):
     """One round (embed, then move every node to the nearest class mean)
     equals the exact-rational computation wherever the nearest mean is
-    clearly nearer than the next one (gap above 1e-4 of the distance; the
-    FP32 distances decide only near-ties)."""
+    nearer than the next one by more than FP64 rounding can blur (gap above
+    1e-9 of the distance), and the oracle's FP64 distances equal the exact
+    ones to 1e-12 relative."""
     rng = np.random.default_rng(seed)
     n, K = 14, 3
     edges = graphgen.random_graph(n, 30, seed=100 + seed)
     Y0 = rng.integers(0, K, n).astype(np.int32)
     Y0[:K] = np.arange(K)  # every class present
-    want, gaps = _exact_round([tuple(e) for e in edges.tolist()], Y0.tolist(), K)
+    want, gaps, dist = _exact_round([tuple(e) for e in edges.tolist()], Y0.tolist(), K)
     got, rounds, moved = oracle.unsupervised(edges, Y0, K, max_iter=1)
     assert rounds == 1 and moved[0] == int(np.sum(got != Y0))
-    clear = [i for i in range(n) if gaps[i] > Fraction(1, 10**4)]
+    clear = [i for i in range(n) if gaps[i] > Fraction(1, 10**9)]
     assert len(clear) >= n // 2
     assert [int(got[i]) for i in clear] == [want[i] for i in clear]
+    nxt, D, T = oracle.unsup_round(edges, Y0, K)
+    assert np.array_equal(nxt, got)
+    for i in range(n):
+        for k in range(K):
+            if dist[i][k] is None:
+                assert D[i, k] == 0.0
+            else:
+                assert abs(D[i, k] - float(dist[i][k])) <= 1e-12 * max(float(dist[i][k]), 1e-300)
+                assert T[i, k] >= D[i, k]
 
 
 def test_unsupervised_recovers_planted_blocks():
