@@ -223,7 +223,7 @@ __global__ void k_rsqrt(const double *__restrict__ d, int64_t n,
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = tid; i < n; i += nthreads) {
         const double x = d[i];
-        r[i] = x > 0.0 ? __frsqrt_rn((float)x) : 0.0f;
+        r[i] = rsqrt_rn32(x);
     }
 }
 

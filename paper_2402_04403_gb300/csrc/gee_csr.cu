@@ -404,7 +404,7 @@ __global__ void k_row_rsqrt(const int64_t *__restrict__ rowptr,
                 d += (double)val[a];
         else
             d = (double)(a1 - a0);
-        r[i] = d > 0.0 ? __frsqrt_rn((float)d) : 0.0f;
+        r[i] = rsqrt_rn32(d);
     }
 }
 
@@ -429,7 +429,7 @@ __global__ void k_hub_rsqrt(const int32_t *__restrict__ hub_row,
         for (int o = 16; o > 0; o >>= 1)
             d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0)
-            r[hub_row[h]] = d > 0.0 ? __frsqrt_rn((float)d) : 0.0f;
+            r[hub_row[h]] = rsqrt_rn32(d);
     }
 }
 

@@ -98,6 +98,16 @@ __device__ __forceinline__ float fixed_to_z(unsigned long long q, double inv,
         static_cast<double>(nk)));
 }
 
+// Laplacian degree factor r = RN32(1/sqrt(d)) of an FP64 degree d: the
+// square root and the reciprocal in FP64 (each correctly rounded), then
+// one rounding to float; 0 for d <= 0 (a node without edges).
+__device__ __forceinline__ float rsqrt_rn32(double d)
+{
+    if (!(d > 0.0))
+        return 0.0f;
+    return __double2float_rn(__ddiv_rn(1.0, __dsqrt_rn(d)));
+}
+
 inline int grid_for(int64_t work, int threads, int max_blocks)
 {
     int64_t b = (work + threads - 1) / threads;
