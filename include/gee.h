@@ -448,11 +448,15 @@ GEE_API void gee_server_destroy(gee_server *srv);
  * array of GEE_NOALLOC_SCRATCH_BYTES in device global memory that belongs to
  * the library image, so every GPU that loads libgee holds those bytes until
  * the process exits.  The first call on a device looks up that array's
- * device address (once per device); make that first call before any stream
- * capture.  n above GEE_NOALLOC_MAX_NODES returns GEE_ERR_UNSUPPORTED.  The
- * array is shared by all calls and keeps the last call's contents (each call
- * clears what must start at zero), so calls whose work overlaps on the GPU
- * race on it: run them one at a time.  No Laplacian variant.
+ * device address (once per device, kept for the life of the process); make
+ * that first call before any stream capture.  A cudaDeviceReset destroys
+ * the context the kept address belongs to, so do not call this entry point
+ * on a device after resetting it.  Each call waits for its stream to
+ * finish, to read the status word back.  n above GEE_NOALLOC_MAX_NODES
+ * returns GEE_ERR_UNSUPPORTED.  The array is shared by all calls and keeps
+ * the last call's contents (each call clears what must start at zero), so
+ * calls whose work overlaps on the GPU race on it: run them one at a time.
+ * No Laplacian variant.
  */
 #define GEE_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define GEE_NOALLOC_MAX_NODES (GEE_NOALLOC_SCRATCH_BYTES - 2048u)

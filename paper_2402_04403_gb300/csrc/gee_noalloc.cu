@@ -36,7 +36,10 @@ std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices];
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// device (the first call on a device does this set-up) and kept for the
+// life of the process: after a cudaDeviceReset it would name memory of the
+// destroyed context, so the header asks callers not to reset a device they
+// use this entry point on.
 cudaError_t scratch_address(unsigned char **out)
 {
     int dev = 0;

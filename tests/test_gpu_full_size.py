@@ -5,8 +5,10 @@ K = 50; all labelled, then 90 % unlabelled) goes through the three calls the
 benchmark times: the resident-graph pass with device Y and Z, the same pass
 writing a page-locked host Z, and the one-shot edge-list call.  R-MAT scale
 24 with float weights in (0, 1] (K = 20, 10 % unlabelled) goes through the
-resident pass plain, in Laplacian form and deterministic, and through the
-widened pass with 32 label vectors.
+resident pass plain, in Laplacian form and deterministic, through the
+widened pass with 32 label vectors, and through the one-shot edge-list call
+with each scatter strategy (plain and Laplacian).  A weighted batch holds a
+hub-heavy R-MAT graph (scale 22) beside small planted-partition graphs.
 
 Rows checked: the 64 of highest degree (hub rows of many chunks) and 4,096
 random ones; the oracle computes just those rows in one pass over the edge
@@ -69,9 +71,13 @@ def _rows_of(Z, r):
 
 
 def _assert_close(got, z64, what):
+    """Within REL_TOL of the FP64 oracle where it is non-zero, exactly zero
+    where it is zero; prints the max relative and absolute errors."""
     nz = z64 != 0
     assert np.all(got[~nz] == 0), what
-    rel = np.abs(got[nz].astype(np.float64) - z64[nz]) / np.abs(z64[nz])
+    err = np.abs(got[nz].astype(np.float64) - z64[nz])
+    rel = err / np.abs(z64[nz])
+    print(f"{what}: max rel err {rel.max():.3e}, max abs err {err.max():.3e}")
     assert rel.max() <= REL_TOL, f"{what}: rel err {rel.max():.3e}"
 
 
@@ -128,3 +134,53 @@ def test_rmat24_float_weights(gee):
         Zm = _rows_of(g.embed_multi(torch.from_numpy(Ys).to(dev), K), r)
         _assert_close(Zm[:, :K], z64m0, f"vector 0 of {L}")
         _assert_close(Zm[:, (L - 1) * K:], z64m1, f"vector {L - 1} of {L}")
+    # the one-shot edge-list call, every strategy that takes this size
+    # (GEE_AUTO's choice included), plain and Laplacian
+    Z = torch.empty((n, K), dtype=torch.float32, device=dev)
+    for strategy in ONE_SHOT_STRATEGIES:
+        for lap, want in ((False, z64), (True, z64l)):
+            gee.embed(ed, Yd, K, weights=wd, laplacian=lap, strategy=strategy, out=Z)
+            _assert_close(_rows_of(Z, r), want, f"one-shot {strategy}, laplacian={lap}")
+
+
+ONE_SHOT_STRATEGIES = ("auto", "atomic", "segmented")
+
+
+def test_weighted_batch_with_a_hub_heavy_graph(gee):
+    """One batch: an R-MAT scale-22 graph with float weights (n = 4.2 M,
+    s = 64 M; hub rows of ~10^5 arcs, so hub cells sum ~10^4 weights each)
+    and 200 small weighted planted-partition graphs.  The R-MAT problem is
+    checked on its top-64 and 4,096 random rows, the small ones in full."""
+    import torch
+    dev = torch.device("cuda", 0)
+    n, s, K, scale, seed = 1 << 22, 1 << 26, 20, 22, 5
+    ed = graphgen.rmat_edges_device(scale, n, 0, s, seed, device=dev)
+    wd = graphgen.weights_device(s, seed + 2, device=dev)
+    Yd = graphgen.labels_device(n, K, seed + 1, 0.1, device=dev)
+    rows = _sample_rows(ed, n, seed=23)
+    probs = [dict(edges=ed, Y=Yd, K=K, weights=wd)]
+    small = []
+    rng = np.random.default_rng(seed)
+    for i in range(200):
+        ni = int(np.exp(rng.uniform(np.log(100), np.log(100000))))
+        Ki = int(rng.integers(2, 33))
+        si = int(ni * rng.uniform(5, 25))
+        e = graphgen.planted_edges(ni, Ki, si, 10.0, seed=4000 + i)
+        Y = graphgen.planted_labels(ni, Ki)
+        w = graphgen.weights(si, seed=5000 + i)
+        small.append((e, Y, Ki, w))
+        probs.append(dict(edges=torch.from_numpy(e).to(dev), Y=torch.from_numpy(Y).to(dev),
+                          K=Ki, weights=torch.from_numpy(w).to(dev)))
+    r, z64 = oracle.embed_rows(ed.cpu().numpy(), Yd.cpu().numpy(), K, rows,
+                               weights=wd.cpu().numpy())
+    Zs = gee.embed_batch(probs)
+    _assert_close(_rows_of(Zs[0], r), z64, "batch: R-MAT scale 22")
+    worst = 0.0
+    for (e, Y, Ki, w), Z in zip(small, Zs[1:]):
+        want = oracle.embed(e, Y, Ki, weights=w)
+        got = Z.cpu().numpy().astype(np.float64)
+        nz = want != 0
+        assert np.all(got[~nz] == 0)
+        worst = max(worst, float((np.abs(got[nz] - want[nz]) / want[nz]).max()))
+    print(f"batch: 200 small graphs, max rel err {worst:.3e}")
+    assert worst <= REL_TOL

@@ -98,16 +98,20 @@ def test_mixed_burst_equals_solo_calls(gee, graphs):
                 if w is None:
                     assert np.array_equal(Z, oracle.embed_counts32(e, Y, K))
                 else:
+                    _close(Z, oracle.embed(e, Y, K, weights=w), "edge-list request vs oracle")
                     solo = gee.embed(_dev(e), _dev(Y), K, weights=_dev(w)).cpu().numpy()
-                    _close(Z, solo, "edge-list request")
+                    _close(Z, solo, "edge-list request vs its solo call")
             else:
                 Y, K, lap = args
                 g = GA if kind == "A" else GB
                 solo = g.embed(_dev(Y), K, laplacian=lap).cpu().numpy()
                 if kind == "B":
                     assert np.array_equal(Z, solo)
+                    assert np.array_equal(Z, oracle.embed_counts32(eB, Y, K))
                 else:
-                    _close(Z, solo, f"re-label {kind} lap={lap}")
+                    _close(Z, oracle.embed(eA, Y, K, weights=wA, laplacian=lap),
+                           f"re-label {kind} lap={lap} vs oracle")
+                    _close(Z, solo, f"re-label {kind} lap={lap} vs its solo call")
     # spot checks against the oracle itself
     Y, K, _ = results[24][1]
     assert np.array_equal(results[24][2][0], oracle.embed_counts32(eB, Y, K))
@@ -240,3 +244,63 @@ def test_multi_group_outputs_page_locked_and_pageable(gee, graphs):
                 outside[a:b] = False
             assert np.all(np.isnan(flat[outside])), (K, L)
         assert srv.stats()["max_group"] == 16
+
+
+def test_requests_overlap_on_the_device(gee, graphs):
+    """Continuous batching, not a queue: a long edge-list request is admitted
+    and running; small requests submitted after it (an edge list and a
+    re-labeling) are admitted to other slots while it runs, finish before it
+    does, and equal the oracle.  The server saw at least two groups in flight
+    at once."""
+    import time
+    import torch
+    (eB, _, nB) = graphs[1]
+    n, s, K = 4_000_000, 48_000_000, 16
+    # the long request's buffers are page-locked, as a serving client's
+    # are: copies from pageable memory would hold the scheduler thread
+    e_big = torch.from_numpy(graphgen.rmat_edges(22, n, 0, s, seed=31)).pin_memory().numpy()
+    Y_big = torch.from_numpy(graphgen.labels(n, K, seed=32)).pin_memory().numpy()
+    Z_out = torch.empty((n, K), dtype=torch.float32).pin_memory().numpy()
+    with gee.Server(streams=4) as srv:
+        gB = srv.add_graph(eB, nB)
+        t_big = time.perf_counter()
+        big = srv.submit(Y_big, K, edges=e_big, out=Z_out)
+        time.sleep(0.005)  # the scheduler admits it on its own slot
+        e_small = graphgen.random_graph(3000, 20000, seed=33)
+        Y_small = graphgen.labels(3000, 5, seed=34, frac_unlabeled=0.1)
+        Y_re = graphgen.labels(nB, 6, seed=35)
+        t_small = time.perf_counter()
+        small = [srv.submit(Y_small, 5, edges=e_small), srv.submit(Y_re, 6, graph=gB)]
+        done_small = []
+        for t in small:
+            Z, lat = srv.wait(t)
+            done_small.append((Z, t_small + lat / 1e3))
+        Z_big, lat_big = srv.wait(big)
+        done_big = t_big + lat_big / 1e3
+        st = srv.stats()
+    assert st["max_concurrent"] >= 2
+    assert st["groups"] >= 3
+    for _, finished in done_small:
+        assert finished < done_big, "a later small request waited for the long one"
+    assert np.array_equal(done_small[0][0], oracle.embed_counts32(e_small, Y_small, 5))
+    assert np.array_equal(done_small[1][0], oracle.embed_counts32(eB, Y_re, 6))
+    rows = np.random.default_rng(36).integers(0, n, 2000)
+    r, _, C = oracle.embed_rows(e_big, Y_big, K, rows, with_counts=True)
+    want = oracle.round_counts(C, oracle.class_counts(Y_big, K))
+    assert np.array_equal(Z_big[r], want)
+
+
+def test_max_concurrent_counts_groups_in_flight(gee, graphs):
+    """A burst of independent edge-list requests larger than one group
+    (max_batch = 2) on four slots keeps more than one group on the GPU."""
+    reqs = _edge_requests(16, seed=7)
+    with gee.Server(streams=4, max_batch=2) as srv:
+        tickets = [srv.submit(Y, K, edges=e, weights=w) for e, w, Y, K in reqs]
+        outs = [srv.wait(t)[0] for t in tickets]
+        st = srv.stats()
+    assert st["groups"] >= 8 and st["max_concurrent"] >= 2
+    for (e, w, Y, K), Z in zip(reqs, outs):
+        if w is None:
+            assert np.array_equal(Z, oracle.embed_counts32(e, Y, K))
+        else:
+            _close(Z, oracle.embed(e, Y, K, weights=w), "burst request vs oracle")

@@ -1,5 +1,6 @@
 """gee_embed_noalloc, the allocation-free edge-list entry point, through the
-C ABI: its output must match gee_embed's on consecutive calls.
+C ABI: its output must match gee_embed's on consecutive calls, and both
+must match the FP64 oracle.
 
 Callers that cannot allocate device memory once running (a service whose
 device memory another allocator divided up at start-up, or code that must
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import graphgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -66,8 +68,10 @@ def test_matches_gee_embed_on_consecutive_calls(gee):
         want = gee.embed(e_d, y_d, K, weights=w_d).cpu().numpy()
         if w is None:
             assert np.array_equal(got, want)
+            assert np.array_equal(got, oracle.embed_counts32(edges, Y, K))
         else:
             _close(got, want)
+            _close(got, oracle.embed(edges, Y, K, weights=w))
 
 
 def test_label_error_is_reported(gee):
