@@ -1071,9 +1071,19 @@ def run_ours(args, w, world, rank, local):
                              "ms_per_step": os_ms,
                              "strategy": gee.pick_strategy(s, n, K),
                              "api": "gee_embed (edge list in, Z out, nothing resident)"}
-        if not g_close_first:
-            # the other one-shot strategy: a temporary CSR and the pull pass
-            other = "segmented" if result["oneshot"]["strategy"] != "segmented" else "atomic"
+        # per-kernel times of one traced call (CUDA events on the stream)
+        gee.profile_read()
+        gee.profile_enable(True)
+        gee.embed(edges, Y, K, weights=wts, laplacian=lap, out=Z)
+        torch.cuda.synchronize()
+        result["oneshot"]["kernels"] = {
+            k: round(v["total_ms"], 3) for k, v in gee.profile_read().items()}
+        gee.profile_enable(False)
+        if not g_close_first or result["oneshot"]["strategy"] == "binned":
+            # another one-shot strategy: the pushed atomics, or a temporary
+            # CSR and the pull pass
+            other = ("atomic" if result["oneshot"]["strategy"] == "binned" else
+                     "segmented" if result["oneshot"]["strategy"] != "segmented" else "atomic")
             gee.embed(edges, Y, K, weights=wts, laplacian=lap, out=Z, strategy=other)
             torch.cuda.synchronize()
             e0.record(stream)

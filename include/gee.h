@@ -82,17 +82,26 @@ typedef enum gee_status {
     GEE_ERR_CANCELLED = 9     /* a server request cancelled before it ran */
 } gee_status;
 
-/* Edge-pass strategy of the edge-list entry points.  AUTO takes the choice
- * gee_autotune measured for the nearest problem shape when the device has a
- * tuning table, else PRIVATE when n*K fits in shared memory and every CTA
- * would merge several edges per cell, ATOMIC otherwise.  SEGMENTED (CSR by
- * row, each Z row written once, no global atomics) is what a gee_graph
- * always uses. */
+/* Edge-pass strategy of the edge-list entry points.  AUTO takes BINNED when
+ * Z has more than 2^24 cells (n*K; beyond the autotuner's grid, where
+ * updates pushed into Z miss L2), else the choice gee_autotune measured for
+ * the nearest problem shape when the device has a tuning table, else
+ * PRIVATE when n*K fits in shared memory and every CTA would merge several
+ * edges per cell, ATOMIC otherwise.  SEGMENTED (CSR by row, each Z row
+ * written once, no global atomics) is what a gee_graph always uses. */
 typedef enum gee_strategy {
     GEE_AUTO = 0,
     GEE_ATOMIC = 1,    /* edge stream, red.global atomics into Z */
     GEE_PRIVATE = 2,   /* per-CTA copy of Z in shared memory, then merged */
-    GEE_SEGMENTED = 3  /* build CSR by row, then one pull pass per row tile */
+    GEE_SEGMENTED = 3, /* build CSR by row, then one pull pass per row tile */
+    GEE_BINNED = 4     /* updates written as records grouped by Z row tile
+                          (two partition passes), each tile summed in shared
+                          memory and written once: no atomics on Z.  Float
+                          sums keep each addition's rounding error beside
+                          them (about one rounding per cell whatever the
+                          row's degree).  Scratch: 6 bytes per update slot
+                          (2s slots), 14 with weights or the Laplacian.
+                          Endpoints are always checked before Z is written. */
 } gee_strategy;
 
 typedef struct gee_options {
@@ -117,8 +126,8 @@ typedef struct gee_options {
                                   order of a rebuilt graph; every arc value is
                                   rounded to a multiple of 2^-S.  Resident-
                                   graph passes and SEGMENTED edge-list calls
-                                  (AUTO then picks SEGMENTED); with ATOMIC or
-                                  PRIVATE, with 8 or more label vectors of a
+                                  (AUTO then picks SEGMENTED); with ATOMIC,
+                                  PRIVATE or BINNED, with 8 or more label vectors of a
                                   weighted graph and in gee_embed_batch for
                                   weighted problems: GEE_ERR_UNSUPPORTED.
                                   Unit weights are exact counts either way. */

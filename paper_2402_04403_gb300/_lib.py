@@ -23,7 +23,7 @@ STATUS_NAMES = {
     9: "GEE_ERR_CANCELLED",
 }
 STATUS = {v: k for k, v in STATUS_NAMES.items()}
-STRATEGIES = {"auto": 0, "atomic": 1, "private": 2, "segmented": 3}
+STRATEGIES = {"auto": 0, "atomic": 1, "private": 2, "segmented": 3, "binned": 4}
 STRATEGY_NAMES = {v: k for k, v in STRATEGIES.items()}
 MAX_CLASSES = 255
 MAX_COLUMNS = 1024

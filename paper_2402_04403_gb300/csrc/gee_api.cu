@@ -129,6 +129,17 @@ gee_status deterministic_strategy(gee_options &o, bool weighted,
     return o.strategy == GEE_SEGMENTED ? GEE_OK : GEE_ERR_UNSUPPORTED;
 }
 
+// Z cells above which GEE_AUTO takes BINNED (the autotuner's grid ends
+// at 2^24 cells).
+constexpr int64_t kBinnedMinCells = int64_t(1) << 24;
+
+bool binned_fits(int64_t n, int32_t K)
+{
+    int32_t coarse = 0, group = 0;
+    const int32_t rows = bin_rows(K, true);
+    return bin_layout((n + rows - 1) / rows, &coarse, &group);
+}
+
 gee_options resolve_options(const gee_options *opts)
 {
     gee_options o;
@@ -391,6 +402,29 @@ gee_status embed_coo(Workspace &ws, const int32_t *E, const float *w,
         int32_t block = 0;
         if (tuned_choice(s, n, K, &tuned, &block) && tuned == strat && block != 0)
             threads = block;
+    }
+    if (strat == GEE_BINNED) {
+        rc = labels_launch(Y, n, K, nullptr, Yc, counts, st, stream);
+        if (rc != GEE_OK)
+            return rc;
+        float *r = nullptr;
+        if (laplacian) {
+            double *d;
+            GEE_CHECK_CUDA(ws.alloc((void **)&d, sizeof(double) * (n + 1)));
+            GEE_CHECK_CUDA(ws.alloc((void **)&r, sizeof(float) * (n + 1)));
+            GEE_CHECK_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (n + 1), stream));
+            if (s > 0) {
+                ProfScope p("k_degree", stream);
+                GEE_CHECK_CUDA(launch_degree(E, w, s, n, d, st, stream));
+            }
+            if (n > 0) {
+                ProfScope p("k_rsqrt", stream);
+                GEE_CHECK_CUDA(launch_rsqrt(d, n, r, st, stream));
+            }
+        }
+        GEE_CHECK_CUDA(launch_binned(ws, E, w, s, n, K, Yc, r, counts, Z, st,
+                                     stream));
+        return GEE_OK;
     }
     if (strat == GEE_SEGMENTED) {
         Csr g;
@@ -701,8 +735,14 @@ gee_strategy gee_pick_strategy(int64_t s, int64_t n, int32_t K,
     const int64_t cells = n * (int64_t)K;
     if (o.strategy == GEE_PRIVATE && cells > limit)
         return GEE_ATOMIC;  // the copy would not fit in shared memory
+    if (o.strategy == GEE_BINNED && !binned_fits(n, K))
+        return GEE_ATOMIC;  // beyond the two-level layout of row tiles
     if (o.strategy != GEE_AUTO)
         return static_cast<gee_strategy>(o.strategy);
+    // past the tuning grid: a Z this large misses L2, so pushing updates
+    // into it costs a DRAM read-modify-write each
+    if (cells > kBinnedMinCells && binned_fits(n, K))
+        return GEE_BINNED;
     gee_strategy tuned;
     int32_t tuned_block = 0;
     if (tuned_choice(s, n, K, &tuned, &tuned_block))
@@ -724,6 +764,11 @@ size_t gee_workspace_bytes(int64_t s, int64_t n, int32_t K, int32_t weighted,
     const gee_strategy st = gee_pick_strategy(s, n, K, opts);
     if (laplacian)
         b += (size_t)(n + 1) * 12;
+    if (st == GEE_BINNED) {
+        const bool wt = weighted || laplacian;
+        const int32_t rows = bin_rows(K, wt);
+        b += bin_scratch_bytes(2 * s, (n + rows - 1) / rows, wt) + 512;
+    }
     if (st == GEE_SEGMENTED) {
         b += (size_t)(n + 1) * (8 * 4 + 4 * 4);  // rowptr, scan and fill temps
         b += (size_t)(2 * s + 8) * 4 * (weighted || laplacian ? 3 : 1);
@@ -776,7 +821,7 @@ gee_status gee_embed(const int32_t *edges, const float *weights, int64_t s,
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
-    if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
+    if (o.strategy < GEE_AUTO || o.strategy > GEE_BINNED)
         return GEE_ERR_INVALID_ARG;
     gee_options oo = o;
     rc = deterministic_strategy(oo, weights != nullptr, laplacian);
@@ -806,7 +851,7 @@ gee_status gee_embed_host(const int32_t *edges_h, const float *weights_h,
         return GEE_ERR_INVALID_ARG;
     if (s > 0 && n == 0)
         return GEE_ERR_NODE_RANGE;
-    if (o.strategy < GEE_AUTO || o.strategy > GEE_SEGMENTED)
+    if (o.strategy < GEE_AUTO || o.strategy > GEE_BINNED)
         return GEE_ERR_INVALID_ARG;
     rc = deterministic_strategy(o, weights_h != nullptr, laplacian);
     if (rc != GEE_OK)

@@ -400,6 +400,70 @@ cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
                                bool validate, cudaStream_t stream,
                                cudaGraphExec_t *exec);
 
+// ------------------------------------------------------------ binned pass
+// GEE_BINNED (gee_bin.cu): updates written out as records grouped by the
+// row tile of Z they land in, each tile summed in shared memory and
+// written once.
+
+// Unsigned 32-bit division by a divisor fixed at launch, by multiplication.
+struct UDiv {
+    uint32_t d, m, s1, s2;
+    void init(uint32_t divisor);
+    __device__ __forceinline__ uint32_t div(uint32_t x) const
+    {
+        const uint32_t t = __umulhi(m, x);
+        return (t + ((x - t) >> s1)) >> s2;
+    }
+};
+
+// One edge-list problem of a binned launch (device copy).
+struct BinProblem {
+    const int32_t *E;           // int32 [s][2]
+    const float *w;             // [s] or null
+    int64_t s, n;
+    const uint8_t *Yc;          // [n] compact labels
+    const float *r;             // [n] Laplacian factors, or null
+    float *Z;                   // [n][K]
+    const uint32_t *counts;     // [K] n_k
+    DevStatus *st;
+    int64_t tile0, tiles;       // its row tiles: global [tile0, tile0 + tiles)
+    int64_t chunk0;             // its first global edge chunk
+    int32_t K, rows;            // classes; rows per tile
+    uint32_t kmagic;            // floor((2^32 - 1) / K) + 1 (K > 1)
+    UDiv rowdiv;                // x -> x / rows
+};
+
+// The launch's sizes and scratch (kernel parameter, by value).
+struct BinPlan {
+    int32_t problems, coarse, group, pad;
+    int64_t tiles, edge_chunks, records;   // records: capacity (2 s)
+    UDiv groupdiv;                          // global tile -> coarse bin
+    unsigned long long *cnt1, *fill1, *off1, *chunk1;  // [coarse + 1]
+    unsigned long long *cnt2, *fill2, *off2;           // [coarse * group + 1]
+    unsigned long long *work;                          // tile counter
+    uint32_t *key1;             // coarse records: tile << 16 | cell
+    float *val1;                // their values (weighted)
+    uint16_t *key2;             // tile records: the cell within the tile
+    float *val2;
+};
+
+// Rows per tile for K classes; false when `tiles` row tiles exceed the
+// two-level layout (about 10^6 tiles).
+int32_t bin_rows(int32_t K, bool weighted);
+bool bin_layout(int64_t tiles, int32_t *coarse, int32_t *group);
+// Scratch of a binned launch over `records` record slots and `tiles` tiles.
+size_t bin_scratch_bytes(int64_t records, int64_t tiles, bool weighted);
+// Enqueues the binned sequence for a problem table already in device
+// memory; pl's sizes set by the caller, its arrays allocated here.
+cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
+                        bool weighted, bool laplacian, cudaStream_t stream);
+// S4 + S5 of one edge list: endpoints checked (GEE_ERR_NODE_RANGE before Z
+// is written), Z written in full.  Yc, counts (and r) from S1-S3.
+cudaError_t launch_binned(Allocator &al, const int32_t *E, const float *w,
+                          int64_t s, int64_t n, int32_t K, const uint8_t *Yc,
+                          const float *r, const uint32_t *counts, float *Z,
+                          DevStatus *st, cudaStream_t stream);
+
 // ------------------------------------------------------------ autotuner
 // The tuned GEE_AUTO choice for an edge-list problem (gee_tune.cu); false
 // when the current device has no table.

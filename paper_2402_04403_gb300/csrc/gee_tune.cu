@@ -102,7 +102,7 @@ gee_status gee_tune_set(const gee_tune_cell *cells, int32_t count)
         return GEE_ERR_INVALID_ARG;
     for (int32_t i = 0; i < count; ++i) {
         const gee_tune_cell &c = cells[i];
-        if (c.strategy < GEE_ATOMIC || c.strategy > GEE_SEGMENTED ||
+        if (c.strategy < GEE_ATOMIC || c.strategy > GEE_BINNED ||
             (c.block != 0 && (c.block % 32 != 0 || c.block < 32 || c.block > 1024)))
             return GEE_ERR_INVALID_ARG;
     }

@@ -71,7 +71,7 @@ def test_zero_nodes(gee):
     e = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
     Y = torch.zeros(0, dtype=torch.int32, device="cuda")
     assert gee.histogram(Y, 4).cpu().tolist() == [0, 0, 0, 0]
-    for strategy in ("atomic", "private", "segmented"):
+    for strategy in ("atomic", "private", "segmented", "binned"):
         for lap in (False, True):
             Z = gee.embed(e, Y, 3, laplacian=lap, strategy=strategy)
             assert tuple(Z.shape) == (0, 3)

@@ -29,7 +29,7 @@ def _small():
     return graphgen.random_graph(n, s, seed=3), graphgen.labels(n, K, seed=4), n, K
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "private", "segmented"])
+@pytest.mark.parametrize("strategy", ["atomic", "private", "segmented", "binned"])
 @pytest.mark.parametrize("bad", [4, -2, 1 << 20])
 def test_label_out_of_range_leaves_z(gee, strategy, bad):
     import torch
@@ -43,7 +43,7 @@ def test_label_out_of_range_leaves_z(gee, strategy, bad):
     assert torch.all(Z == 3.5)
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "private", "segmented"])
+@pytest.mark.parametrize("strategy", ["atomic", "private", "segmented", "binned"])
 @pytest.mark.parametrize("laplacian", [False, True])
 def test_node_out_of_range_leaves_z(gee, strategy, laplacian):
     import torch
@@ -85,7 +85,7 @@ def test_laplacian_rejects_negative_weights(gee):
     edges, Y, n, K = _small()
     w = graphgen.weights(edges.shape[0], seed=1).copy()
     w[10] = -0.5
-    for st in ("atomic", "segmented"):
+    for st in ("atomic", "segmented", "binned"):
         with pytest.raises(gee.GeeError) as ei:
             gee.embed(_dev(edges), _dev(Y), K, weights=_dev(w), laplacian=True, strategy=st)
         assert ei.value.name == "GEE_ERR_INVALID_ARG"

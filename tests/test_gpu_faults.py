@@ -37,7 +37,7 @@ def test_injected_allocation_failures(gee):
     Y = graphgen.labels(n, K, seed=4, frac_unlabeled=0.1)
     want = oracle.embed_counts32(e, Y, K)
     try:
-        for strategy in ("atomic", "segmented"):
+        for strategy in ("atomic", "segmented", "binned"):
             gee.debug_fail_allocs(1)
             with pytest.raises(gee.GeeError) as ei:
                 gee.embed(_dev(e), _dev(Y), K, strategy=strategy)

@@ -143,7 +143,7 @@ def test_rmat24_float_weights(gee):
             _assert_close(_rows_of(Z, r), want, f"one-shot {strategy}, laplacian={lap}")
 
 
-ONE_SHOT_STRATEGIES = ("auto", "atomic", "segmented")
+ONE_SHOT_STRATEGIES = ("auto", "atomic", "segmented", "binned")
 
 
 def test_weighted_batch_with_a_hub_heavy_graph(gee):

@@ -15,7 +15,7 @@ from tests import _pins
 pytestmark = pytest.mark.gpu
 
 REL_TOL = 1e-5
-STRATEGIES = ["atomic", "private", "segmented"]
+STRATEGIES = ["atomic", "private", "segmented", "binned"]
 
 
 @pytest.fixture(scope="module")
