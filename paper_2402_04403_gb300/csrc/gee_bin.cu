@@ -220,10 +220,10 @@ __global__ void __launch_bounds__(kEdgeThreads)
                 report(p.st, GEE_ERR_NODE_RANGE, (unsigned long long)e);
                 continue;
             }
-            bump(pl.groupdiv.div(
-                (uint32_t)p.tile0 + p.rowdiv.div((uint32_t)uv[j].x)));
-            bump(pl.groupdiv.div(
-                (uint32_t)p.tile0 + p.rowdiv.div((uint32_t)uv[j].y)));
+            bump(((uint32_t)p.tile0 + ((uint32_t)uv[j].x >> p.row_shift)) >>
+                 pl.group_shift);
+            bump(((uint32_t)p.tile0 + ((uint32_t)uv[j].y >> p.row_shift)) >>
+                 pl.group_shift);
         }
     }
     if (run != 0u)
@@ -301,9 +301,10 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
     constexpr int kRec = 2 * kEdgeChunk;
     uint32_t *hist = reinterpret_cast<uint32_t *>(sm);  // counts, then cursors
     uint32_t *start = hist + kMaxBins;
-    unsigned long long *base =
+    // dst0[b] + i: where staged record i of bin b goes in the coarse records
+    unsigned long long *dst0 =
         reinterpret_cast<unsigned long long *>(start + kMaxBins);
-    uint32_t *skey = reinterpret_cast<uint32_t *>(base + kMaxBins);
+    uint32_t *skey = reinterpret_cast<uint32_t *>(dst0 + kMaxBins);
     float *sval = reinterpret_cast<float *>(skey + kRec);
     uint16_t *sbin =
         reinterpret_cast<uint16_t *>(sval + (WEIGHTED ? kRec : 0));
@@ -321,6 +322,7 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
         const int64_t e0 = (chunk - p.chunk0) * kEdgeChunk;
         const int64_t e1 = min(e0 + (int64_t)kEdgeChunk, p.s);
         const int2 *E = reinterpret_cast<const int2 *>(p.E);
+        const uint32_t rs = p.row_shift, gs = pl.group_shift;
         const uint32_t rows = (uint32_t)p.rows, K = (uint32_t)p.K,
                        tile0 = (uint32_t)p.tile0;
         int2 uv[kEdgesPerThread];
@@ -353,10 +355,9 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
             const int j = i >> 1;
             const uint32_t row = (uint32_t)((i & 1) ? uv[j].y : uv[j].x);
             const uint32_t y = (i & 1) ? (y2[j] & 0xFFu) : (y2[j] >> 8);
-            const uint32_t lt = p.rowdiv.div(row);  // tile within the problem
-            const uint32_t g = tile0 + lt;
-            c = pl.groupdiv.div(g);
-            key = ((g - c * G) << 16) | ((row - lt * rows) * K + y);
+            const uint32_t g = tile0 + (row >> rs);  // global row tile
+            c = g >> gs;
+            key = ((g & (G - 1u)) << 16) | ((row & (rows - 1u)) * K + y);
             return y != kNoLabel;
         };
 #pragma unroll
@@ -367,12 +368,21 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
         }
         __syncthreads();
         scan_bins<kEdgeThreads>(hist, start, B, warp_tot, &s_total);
-        for (int b = threadIdx.x; b < B; b += blockDim.x) {
-            const uint32_t h = hist[b];
-            if (h != 0u)
-                base[b] = pl.off1[b] +
-                          atomicAdd(pl.fill1 + b, (unsigned long long)h);
-            hist[b] = start[b];  // cursor of the staging area
+        // reserve each bin's run in its coarse bin; the atomics' results
+        // are needed only by the write-out, so they stay in flight while
+        // the records are staged
+        constexpr int kResv = kMaxBins / kEdgeThreads;
+        unsigned long long resv[kResv];
+#pragma unroll
+        for (int i = 0; i < kResv; ++i) {
+            const int b = threadIdx.x + i * kEdgeThreads;
+            resv[i] = 0ull;
+            if (b < B) {
+                const uint32_t h = hist[b];
+                if (h != 0u)
+                    resv[i] = atomicAdd(pl.fill1 + b, (unsigned long long)h);
+                hist[b] = start[b];  // cursor of the staging area
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -390,11 +400,16 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i < kResv; ++i) {
+            const int b = threadIdx.x + i * kEdgeThreads;
+            if (b < B)  // unsigned wrap-around cancels when i is added
+                dst0[b] = pl.off1[b] + resv[i] - start[b];
+        }
         __syncthreads();
         const uint32_t total = s_total;
         for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-            const uint32_t b = sbin[i];
-            const unsigned long long dst = base[b] + (i - start[b]);
+            const unsigned long long dst = dst0[sbin[i]] + i;
             __stcs(pl.key1 + dst, skey[i]);
             if (WEIGHTED)
                 __stcs(pl.val1 + dst, sval[i]);
@@ -476,12 +491,13 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
     __shared__ unsigned long long s_r0, s_r1;
     uint32_t *hist = reinterpret_cast<uint32_t *>(sm);  // counts, then cursors
     uint32_t *start = hist + kMaxBins;
-    unsigned long long *base =
+    // dst0[f] + i: where staged record i of tile f goes in the tile records
+    unsigned long long *dst0 =
         reinterpret_cast<unsigned long long *>(start + kMaxBins);
-    float *sval = reinterpret_cast<float *>(base + kMaxBins);
-    uint16_t *skey =
-        reinterpret_cast<uint16_t *>(sval + (WEIGHTED ? kRecChunk : 0));
-    uint16_t *sfine = skey + kRecChunk;
+    float *sval = reinterpret_cast<float *>(dst0 + kMaxBins);
+    // staged record: cell | tile << 16
+    uint32_t *sent =
+        reinterpret_cast<uint32_t *>(sval + (WEIGHTED ? kRecChunk : 0));
     const int G = pl.group;
     for (int f = threadIdx.x; f < G; f += blockDim.x)
         hist[f] = 0u;
@@ -516,14 +532,19 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
         }
         __syncthreads();
         scan_bins<kRecThreads>(hist, start, G, warp_tot, &s_total);
-        for (int f = threadIdx.x; f < G; f += blockDim.x) {
-            const uint32_t h = hist[f];
-            if (h != 0u) {
-                const int64_t t = (int64_t)c * G + f;
-                base[f] = pl.off2[t] +
-                          atomicAdd(pl.fill2 + t, (unsigned long long)h);
+        constexpr int kResv = kMaxBins / kRecThreads;
+        unsigned long long resv[kResv];
+#pragma unroll
+        for (int i = 0; i < kResv; ++i) {
+            const int f = threadIdx.x + i * kRecThreads;
+            resv[i] = 0ull;
+            if (f < G) {
+                const uint32_t h = hist[f];
+                if (h != 0u)
+                    resv[i] = atomicAdd(pl.fill2 + (int64_t)c * G + f,
+                                        (unsigned long long)h);
+                hist[f] = start[f];
             }
-            hist[f] = start[f];
         }
         __syncthreads();
 #pragma unroll
@@ -532,18 +553,23 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
             const uint32_t f = ok ? key[q] >> 16 : 0u;
             const uint32_t pos = take_in_bin(ok, f, hist);
             if (ok) {
-                skey[pos] = (uint16_t)(key[q] & 0xFFFFu);
-                sfine[pos] = (uint16_t)f;
+                sent[pos] = key[q];  // the coarse key: tile << 16 | cell
                 if (WEIGHTED)
                     sval[pos] = val[q];
             }
         }
+#pragma unroll
+        for (int i = 0; i < kResv; ++i) {
+            const int f = threadIdx.x + i * kRecThreads;
+            if (f < G)  // unsigned wrap-around cancels when i is added
+                dst0[f] = pl.off2[(int64_t)c * G + f] + resv[i] - start[f];
+        }
         __syncthreads();
         const uint32_t total = s_total;
         for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-            const uint32_t f = sfine[i];
-            const unsigned long long dst = base[f] + (i - start[f]);
-            pl.key2[dst] = skey[i];
+            const uint32_t e = sent[i];
+            const unsigned long long dst = dst0[e >> 16] + i;
+            pl.key2[dst] = (uint16_t)(e & 0xFFFFu);
             if (WEIGHTED)
                 __stcs(pl.val2 + dst, sval[i]);
         }
@@ -705,15 +731,51 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int zq = (cells - zh) >> 2;
         if ((int)threadIdx.x < zh)
             __stcs(z + threadIdx.x, value(threadIdx.x, class_of(threadIdx.x)));
+        // quads of cells: acc[off + j0] is 16-byte aligned (off + zh is a
+        // multiple of 4); read and cleared whole, all-zero quads (isolated
+        // rows, classes a row never sees) skip the conversion
         for (int q = threadIdx.x; q < zq; q += blockDim.x) {
             const int j0 = zh + 4 * q;
-            int k = class_of(j0);
-            float o[4];
+            float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (WEIGHTED) {
+                float4 *a4 = reinterpret_cast<float4 *>(accw + off + j0);
+                const float4 c01 = a4[0], c23 = a4[1];
+                const float hi[4] = {c01.x, c01.z, c23.x, c23.z};
+                const float lo[4] = {c01.y, c01.w, c23.y, c23.w};
+                if ((hi[0] != 0.0f) | (hi[1] != 0.0f) | (hi[2] != 0.0f) |
+                    (hi[3] != 0.0f) | (lo[0] != 0.0f) | (lo[1] != 0.0f) |
+                    (lo[2] != 0.0f) | (lo[3] != 0.0f)) {
+                    a4[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    a4[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    int k = class_of(j0);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                o[e] = value(j0 + e, k);
-                if (++k == K)
-                    k = 0;
+                    for (int e = 0; e < 4; ++e) {
+                        float v = sum_to_z(__fadd_rn(hi[e], lo[e]), nk[k]);
+                        if (LAP)
+                            v = __fmul_rn(v, __ldg(p.r + r0 + row_of(j0 + e)));
+                        o[e] = v;
+                        if (++k == K)
+                            k = 0;
+                    }
+                }
+            } else {
+                uint4 *a4 = reinterpret_cast<uint4 *>(acc + off + j0);
+                const uint4 c4 = *a4;
+                if ((c4.x | c4.y | c4.z | c4.w) != 0u) {
+                    *a4 = make_uint4(0u, 0u, 0u, 0u);
+                    const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+                    int k = class_of(j0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t c = cs[e];
+                        o[e] = c == 0u ? 0.0f
+                               : c < (uint32_t)kTablePerClass
+                                   ? table[k * kTablePerClass + c]
+                                   : count_to_z(c, nk[k]);
+                        if (++k == K)
+                            k = 0;
+                    }
+                }
             }
             __stcs(reinterpret_cast<float4 *>(z + j0),
                    make_float4(o[0], o[1], o[2], o[3]));
@@ -741,8 +803,7 @@ size_t edges_smem(bool weighted)
 
 size_t split_smem(bool weighted)
 {
-    return kMaxBins * (4 + 4 + 8) +
-           (size_t)kRecChunk * (2 + 2 + (weighted ? 4 : 0));
+    return kMaxBins * (4 + 4 + 8) + (size_t)kRecChunk * (4 + (weighted ? 4 : 0));
 }
 
 size_t tiles_smem(bool weighted)
@@ -755,26 +816,13 @@ size_t tiles_smem(bool weighted)
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-void UDiv::init(uint32_t dv)
-{
-    // Granlund and Montgomery, "Division by invariant integers using
-    // multiplication" (PLDI 1994), Figure 4.1: with l = ceil(log2 d),
-    // m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((x - t) >> 1)) >> (l - 1)
-    // where t = mulhi(m, x), exact for every 32-bit x (shifts clamped for
-    // d = 1).
-    d = dv;
-    uint32_t l = 0;
-    while (l < 32 && (1ull << l) < (unsigned long long)dv)
-        ++l;
-    m = (uint32_t)(((((1ull << l) - dv) << 32) / dv) + 1ull);
-    s1 = l < 1 ? l : 1;
-    s2 = l > 1 ? l - 1 : 0;
-}
-
 int32_t bin_rows(int32_t K, bool weighted)
 {
     const int cells = weighted ? kTileBytes / 8 : kTileBytes / 4;
-    return cells / K;
+    int32_t r = 1;
+    while (2 * r * K <= cells)
+        r *= 2;
+    return r;
 }
 
 bool bin_layout(int64_t tiles, int32_t *coarse, int32_t *group)
@@ -785,7 +833,7 @@ bool bin_layout(int64_t tiles, int32_t *coarse, int32_t *group)
         return false;
     int64_t g = 1;
     while (g * g < tiles)
-        ++g;
+        g *= 2;
     const int64_t c = (tiles + g - 1) / g;
     *group = (int32_t)g;
     *coarse = (int32_t)c;
@@ -945,7 +993,7 @@ cudaError_t launch_binned(Allocator &al, const int32_t *E, const float *w,
     hp.st = st;
     hp.K = K;
     hp.rows = bin_rows(K, weighted);
-    hp.rowdiv.init((uint32_t)hp.rows);
+    hp.row_shift = (uint32_t)__builtin_ctz((unsigned)hp.rows);
     hp.kmagic = K > 1 ? (uint32_t)(0xFFFFFFFFull / (uint32_t)K + 1ull) : 0u;
     hp.tile0 = 0;
     hp.tiles = (n + hp.rows - 1) / hp.rows;
@@ -957,7 +1005,7 @@ cudaError_t launch_binned(Allocator &al, const int32_t *E, const float *w,
     pl.records = 2 * s;
     if (!bin_layout(pl.tiles, &pl.coarse, &pl.group))
         return cudaErrorInvalidValue;
-    pl.groupdiv.init((uint32_t)pl.group);
+    pl.group_shift = (uint32_t)__builtin_ctz((unsigned)pl.group);
     BinProblem *dP = nullptr;
     cudaError_t e = al.alloc((void **)&dP, sizeof(BinProblem));
     if (e == cudaSuccess)

@@ -405,17 +405,6 @@ cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
 // row tile of Z they land in, each tile summed in shared memory and
 // written once.
 
-// Unsigned 32-bit division by a divisor fixed at launch, by multiplication.
-struct UDiv {
-    uint32_t d, m, s1, s2;
-    void init(uint32_t divisor);
-    __device__ __forceinline__ uint32_t div(uint32_t x) const
-    {
-        const uint32_t t = __umulhi(m, x);
-        return (t + ((x - t) >> s1)) >> s2;
-    }
-};
-
 // One edge-list problem of a binned launch (device copy).
 struct BinProblem {
     const int32_t *E;           // int32 [s][2]
@@ -428,16 +417,16 @@ struct BinProblem {
     DevStatus *st;
     int64_t tile0, tiles;       // its row tiles: global [tile0, tile0 + tiles)
     int64_t chunk0;             // its first global edge chunk
-    int32_t K, rows;            // classes; rows per tile
+    int32_t K, rows;            // classes; rows per tile (a power of two)
     uint32_t kmagic;            // floor((2^32 - 1) / K) + 1 (K > 1)
-    UDiv rowdiv;                // x -> x / rows
+    uint32_t row_shift;         // log2(rows)
 };
 
 // The launch's sizes and scratch (kernel parameter, by value).
 struct BinPlan {
     int32_t problems, coarse, group, pad;
     int64_t tiles, edge_chunks, records;   // records: capacity (2 s)
-    UDiv groupdiv;                          // global tile -> coarse bin
+    uint32_t group_shift, pad2;             // log2(group): tile -> coarse bin
     unsigned long long *cnt1, *fill1, *off1, *chunk1;  // [coarse + 1]
     unsigned long long *cnt2, *fill2, *off2;           // [coarse * group + 1]
     unsigned long long *work;                          // tile counter
@@ -447,8 +436,10 @@ struct BinPlan {
     float *val2;
 };
 
-// Rows per tile for K classes; false when `tiles` row tiles exceed the
-// two-level layout (about 10^6 tiles).
+// Rows per tile for K classes: the largest power of two whose cells fit
+// a tile's accumulators (so rows and bins split by shifts); bin_layout is
+// false when `tiles` row tiles exceed the two-level layout (about 10^6
+// tiles).  group is a power of two.
 int32_t bin_rows(int32_t K, bool weighted);
 bool bin_layout(int64_t tiles, int32_t *coarse, int32_t *group);
 // Scratch of a binned launch over `records` record slots and `tiles` tiles.
