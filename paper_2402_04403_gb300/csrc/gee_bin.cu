@@ -155,23 +155,10 @@ __device__ __forceinline__ void scan_bins(const uint32_t *h, uint32_t *start,
     __syncthreads();
 }
 
-// A record's bin counted (count_in_bin), then its slot taken from the
-// bin's cursor (take_in_bin).  Plain shared-memory atomics: lanes that
-// share a bin are serialised by the hardware, which costs less than
-// grouping them first (match.any runs at about one lane per two SM clocks
-// on GB300, shared-memory atomics at six or more).
-__device__ __forceinline__ void count_in_bin(bool valid, uint32_t bin,
-                                             uint32_t *hist)
-{
-    if (valid)
-        atomicAdd(hist + bin, 1u);
-}
-
-__device__ __forceinline__ uint32_t take_in_bin(bool valid, uint32_t bin,
-                                                uint32_t *cursor)
-{
-    return valid ? atomicAdd(cursor + bin, 1u) : 0u;
-}
+// Ranks within a bin come from plain shared-memory atomics (one per
+// record): lanes that share a bin are serialised by the hardware, which
+// costs less than grouping them first (match.any runs at about one lane per
+// two SM clocks on GB300, shared-memory atomics at six or more).
 
 // ---------------------------------------------------------------- counts
 // Per coarse bin, an upper bound of its records: both endpoints of every
@@ -291,7 +278,7 @@ __global__ void __launch_bounds__(1024)
 // A record is its row tile within the coarse bin (high 16 bits) and its
 // cell within the tile (low 16 bits); the weighted form keeps the value in
 // a parallel float array.
-template <bool WEIGHTED, bool LAP>
+template <bool WEIGHTED, bool LAP, bool WIDE>
 __global__ void __launch_bounds__(kEdgeThreads, 2)
     k_bin_edges(BinPlan pl, const BinProblem *P)
 {
@@ -350,22 +337,44 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
             }
         }
         // record i: row u with v's class (even i), row v with u's (odd i);
-        // none where that class is unknown
-        auto record = [&](int i, uint32_t &c, uint32_t &key) -> bool {
+        // key 0xFFFFFFFF where that class is unknown.  The key holds the
+        // whole tile number while it fits 16 bits (the bin is then
+        // key >> (16 + gs)), else the tile within the bin, with the bin
+        // kept beside it (16-bit halves of cw).  Each record's place among
+        // this chunk's records of its bin comes from one shared-memory
+        // atomic (16-bit halves of rk).
+        uint32_t key[2 * kEdgesPerThread], rk[kEdgesPerThread];
+        uint32_t cw[WIDE ? kEdgesPerThread : 1];
+        float val[(WEIGHTED && LAP) ? 2 * kEdgesPerThread : 1];
+#pragma unroll
+        for (int i = 0; i < 2 * kEdgesPerThread; ++i) {
             const int j = i >> 1;
             const uint32_t row = (uint32_t)((i & 1) ? uv[j].y : uv[j].x);
             const uint32_t y = (i & 1) ? (y2[j] & 0xFFu) : (y2[j] >> 8);
             const uint32_t g = tile0 + (row >> rs);  // global row tile
-            c = g >> gs;
-            key = ((g & (G - 1u)) << 16) | ((row & (rows - 1u)) * K + y);
-            return y != kNoLabel;
-        };
-#pragma unroll
-        for (int i = 0; i < 2 * kEdgesPerThread; ++i) {
-            uint32_t c, key;
-            const bool valid = record(i, c, key);
-            count_in_bin(valid, valid ? c : 0u, hist);
+            const uint32_t c = g >> gs;
+            const bool valid = y != kNoLabel;
+            key[i] = valid ? (((WIDE ? (g & (G - 1u)) : g) << 16) |
+                              ((row & (rows - 1u)) * K + y))
+                           : 0xFFFFFFFFu;
+            if (WIDE) {
+                if (i & 1)
+                    cw[j] |= c << 16;
+                else
+                    cw[j] = c;
+            }
+            if (WEIGHTED && LAP)
+                val[i] = __fmul_rn(wt[j], (i & 1) ? ru[j] : rv[j]);
+            const uint32_t r = valid ? atomicAdd(hist + c, 1u) : 0u;
+            if (i & 1)
+                rk[j] |= r << 16;
+            else
+                rk[j] = r;
         }
+        auto bin_of = [&](int i) -> uint32_t {
+            return WIDE ? ((cw[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)
+                        : (key[i] >> (16 + gs));
+        };
         __syncthreads();
         scan_bins<kEdgeThreads>(hist, start, B, warp_tot, &s_total);
         // reserve each bin's run in its coarse bin; the atomics' results
@@ -381,23 +390,19 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
                 const uint32_t h = hist[b];
                 if (h != 0u)
                     resv[i] = atomicAdd(pl.fill1 + b, (unsigned long long)h);
-                hist[b] = start[b];  // cursor of the staging area
             }
         }
-        __syncthreads();
 #pragma unroll
         for (int i = 0; i < 2 * kEdgesPerThread; ++i) {
-            uint32_t c, key;
-            const bool valid = record(i, c, key);
-            const uint32_t pos = take_in_bin(valid, valid ? c : 0u, hist);
-            if (valid) {
-                skey[pos] = key;
-                sbin[pos] = (uint16_t)c;
-                if (WEIGHTED) {
-                    const int j = i >> 1;
-                    sval[pos] = LAP ? __fmul_rn(wt[j], (i & 1) ? ru[j] : rv[j])
-                                    : wt[j];
-                }
+            if (key[i] != 0xFFFFFFFFu) {
+                const uint32_t c = bin_of(i);
+                const uint32_t pos =
+                    start[c] + ((rk[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                skey[pos] = key[i];
+                if (WIDE)
+                    sbin[pos] = (uint16_t)c;
+                if (WEIGHTED)
+                    sval[pos] = LAP ? val[i] : wt[i >> 1];
             }
         }
 #pragma unroll
@@ -409,8 +414,10 @@ __global__ void __launch_bounds__(kEdgeThreads, 2)
         __syncthreads();
         const uint32_t total = s_total;
         for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-            const unsigned long long dst = dst0[sbin[i]] + i;
-            __stcs(pl.key1 + dst, skey[i]);
+            const uint32_t k1 = skey[i];
+            const unsigned long long dst =
+                dst0[WIDE ? (uint32_t)sbin[i] : (k1 >> (16 + gs))] + i;
+            __stcs(pl.key1 + dst, k1);
             if (WEIGHTED)
                 __stcs(pl.val1 + dst, sval[i]);
         }
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(kRecThreads) k_bin_fine(BinPlan pl)
         for (int q = 0; q < kRecsPerThread; ++q) {
             if (key[q] == 0xFFFFFFFFu)
                 continue;
-            const uint32_t f = key[q] >> 16;
+            const uint32_t f = (key[q] >> 16) & (uint32_t)(G - 1);
             if (f == last && run != 0u) {
                 ++run;
                 continue;
@@ -525,10 +532,19 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
             if (WEIGHTED)
                 val[q] = ok ? __ldcs(pl.val1 + r) : 0.0f;
         }
+        // each record's place among this chunk's records of its tile, kept
+        // as 16-bit halves; the record's tile within the coarse bin is
+        // (key >> 16) & (G - 1) for both coarse key forms
+        const uint32_t gm = (uint32_t)(G - 1);
+        uint32_t rk[kRecsPerThread / 2];
 #pragma unroll
         for (int q = 0; q < kRecsPerThread; ++q) {
             const bool ok = key[q] != 0xFFFFFFFFu;
-            count_in_bin(ok, ok ? key[q] >> 16 : 0u, hist);
+            const uint32_t r = ok ? atomicAdd(hist + ((key[q] >> 16) & gm), 1u) : 0u;
+            if (q & 1)
+                rk[q >> 1] |= r << 16;
+            else
+                rk[q >> 1] = r;
         }
         __syncthreads();
         scan_bins<kRecThreads>(hist, start, G, warp_tot, &s_total);
@@ -543,17 +559,16 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
                 if (h != 0u)
                     resv[i] = atomicAdd(pl.fill2 + (int64_t)c * G + f,
                                         (unsigned long long)h);
-                hist[f] = start[f];
             }
         }
-        __syncthreads();
 #pragma unroll
         for (int q = 0; q < kRecsPerThread; ++q) {
             const bool ok = key[q] != 0xFFFFFFFFu;
-            const uint32_t f = ok ? key[q] >> 16 : 0u;
-            const uint32_t pos = take_in_bin(ok, f, hist);
             if (ok) {
-                sent[pos] = key[q];  // the coarse key: tile << 16 | cell
+                const uint32_t f = (key[q] >> 16) & gm;
+                const uint32_t pos =
+                    start[f] + ((rk[q >> 1] >> (16 * (q & 1))) & 0xFFFFu);
+                sent[pos] = (f << 16) | (key[q] & 0xFFFFu);
                 if (WEIGHTED)
                     sval[pos] = val[q];
             }
@@ -902,23 +917,25 @@ cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
     if (pl.edge_chunks > 0) {
         ProfScope p("k_bin_edges", stream);
         const size_t sm_b = edges_smem(weighted);
-        if (!weighted) {
-            if ((e = with_smem(k_bin_edges<false, false>, sm_b)) != cudaSuccess)
-                return e;
-            k_bin_edges<false, false>
-                <<<grid(pl.edge_chunks, 2), kEdgeThreads, sm_b, stream>>>(pl, dP);
-        } else if (!laplacian) {
-            if ((e = with_smem(k_bin_edges<true, false>, sm_b)) != cudaSuccess)
-                return e;
-            k_bin_edges<true, false>
-                <<<grid(pl.edge_chunks, 2), kEdgeThreads, sm_b, stream>>>(pl, dP);
-        } else {
-            if ((e = with_smem(k_bin_edges<true, true>, sm_b)) != cudaSuccess)
-                return e;
-            k_bin_edges<true, true>
-                <<<grid(pl.edge_chunks, 2), kEdgeThreads, sm_b, stream>>>(pl, dP);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess)
+        const int blocks = grid(pl.edge_chunks, 2);
+        // record keys hold the whole tile number up to 2^16 tiles
+        const bool wide = pl.tiles > 65536;
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t r = with_smem(kern, sm_b);
+            if (r == cudaSuccess)
+                kern<<<blocks, kEdgeThreads, sm_b, stream>>>(pl, dP);
+            return r;
+        };
+        if (!weighted)
+            e = wide ? go(k_bin_edges<false, false, true>)
+                     : go(k_bin_edges<false, false, false>);
+        else if (!laplacian)
+            e = wide ? go(k_bin_edges<true, false, true>)
+                     : go(k_bin_edges<true, false, false>);
+        else
+            e = wide ? go(k_bin_edges<true, true, true>)
+                     : go(k_bin_edges<true, true, false>);
+        if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess)
             return e;
     }
     {

@@ -157,3 +157,24 @@ def test_errors_leave_z(gee, rmat20):
         with pytest.raises(gee.GeeError) as ei:
             gee.embed(_dev(e2), _dev(Y), K, strategy="binned", validate_edges=validate, out=Z)
         assert ei.value.name == "GEE_ERR_NODE_RANGE" and torch.all(Z == 4.5)
+
+
+def test_more_than_65536_tiles(gee):
+    """K = 255 on 9 M nodes: 128 rows per tile, about 70,000 tiles, past
+    the 16 bits that otherwise carry the whole tile number in a record
+    (the wide record form).  Sampled rows (the 64 of highest degree and
+    4,096 random ones) bit-exact against the oracle's counts."""
+    import torch
+    n, s, K = 9_000_000, 20_000_000, 255
+    edges = graphgen.rmat_edges(24, n, 0, s, seed=95)
+    Y = graphgen.labels(n, K, seed=96, frac_unlabeled=0.1)
+    e_d = _dev(edges)
+    Z = gee.embed(e_d, _dev(Y), K, strategy="binned")
+    deg = torch.bincount(e_d.reshape(-1).long(), minlength=n)
+    top = torch.topk(deg, 64).indices.cpu().numpy()
+    rows = np.unique(np.concatenate(
+        [top, np.random.default_rng(97).integers(0, n, 4096)]))
+    r, _, C = oracle.embed_rows(edges, Y, K, rows, with_counts=True)
+    want = oracle.round_counts(C, oracle.class_counts(Y, K))
+    got = Z[torch.from_numpy(r).cuda()].cpu().numpy()
+    assert np.array_equal(got, want)
