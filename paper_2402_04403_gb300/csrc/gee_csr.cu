@@ -716,8 +716,13 @@ struct TileCells {
 // and single arcs for the head and tail.  cells maps (arc, label) to an
 // accumulator index; arcs whose label is unknown go to this thread's own
 // sink cell (no branch, no shared-address contention).
+// SPAN (row tiles): instead of a scalar head and tail, every 16-byte group
+// that overlaps the arcs is loaded and the arcs outside [0, NA) are
+// skipped, so a tile runs no scalar row searches (column arrays carry 4
+// entries of padding past their end).  HOT: a shared-memory copy of the
+// first hot_n labels is consulted first (hub chunks).
 template <bool WEIGHTED, bool MULTI, int NT, class Cells, int UNROLL = kUnroll,
-          bool FIXED = false>
+          bool FIXED = false, bool SPAN = false, bool HOT = false>
 __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            const int32_t *colp,
                                            const float *valp, int NA, int t,
@@ -775,10 +780,46 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
     auto fetch = [&](int32_t v) -> uint32_t {
         if (MULTI)
             return (uint32_t)v;
-        if (v < hot_n)
+        if (HOT && v < hot_n)
             return (uint32_t)hot[v];
         return v < a.cold_from ? label_of(a, v) : cold_label_of(a, v);
     };
+    if constexpr (SPAN) {
+        static_assert(UNROLL == 4, "one quad per thread per round");
+        const int pre = (int)((reinterpret_cast<uintptr_t>(colp) >> 2) & 3);
+        const int4 *col4 = reinterpret_cast<const int4 *>(colp - pre);
+        const float4 *val4 = reinterpret_cast<const float4 *>(valp - pre);
+        const int nq = (NA + pre + 3) >> 2;
+        auto load = [&](int q, int4 &c, float4 &w) {
+            const bool ok = q < nq;
+            c = ok ? __ldcs(col4 + q) : make_int4(0, 0, 0, 0);
+            if (WEIGHTED)
+                w = ok ? __ldcs(val4 + q) : make_float4(0, 0, 0, 0);
+        };
+        int4 c;
+        float4 w;
+        load(t, c, w);
+        for (int q = t; q < nq; q += NT) {
+            int4 cn;
+            float4 wn;
+            load(q + NT, cn, wn);  // next round's arcs, in flight now
+            const int i0 = 4 * q - pre;
+            const int cv[4] = {c.x, c.y, c.z, c.w};
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+            uint32_t y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                y[e] = (i0 + e >= 0 && i0 + e < NA) ? fetch(cv[e]) : kNoLabel;
+            cells.at(i0 > 0 ? i0 : 0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i0 + e >= 0 && i0 + e < NA)
+                    add(i0 + e, y[e], WEIGHTED ? wv[e] : 0.0f);
+            c = cn;
+            w = wn;
+        }
+        return;
+    }
     const int head =
         min((int)((4 - ((reinterpret_cast<uintptr_t>(colp) >> 2) & 3)) & 3), NA);
     if (t < head) {
@@ -891,15 +932,18 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     uint32_t *acc = reinterpret_cast<uint32_t *>(gs + a.acc_off);
     const int64_t g0 = (int64_t)tr.r0 * K;  // first Z cell of the tile
     // acc[off + j] holds cell g0 + j, off = the cell's float offset within
-    // its 128-byte line of Z (any 4-byte aligned Z)
-    const int off = line_offset(a.Z + g0);
+    // the unit its stores start at (any 4-byte aligned Z): a 128-byte line
+    // for page-locked host Z (GT = kHostGroup), which the host link needs
+    // whole; 16 bytes for device Z, where whole lines do not matter to HBM
+    constexpr int kAlign = GT == kHostGroup ? kLineFloats : 4;
+    const int off = line_offset(a.Z + g0) & (kAlign - 1);
     const int cells = NR * K;
     const int NA = NR > 0 ? rp[NR] : 0;
 
     // sweep: the row of arc i is the last row starting at or before i
     if (NA > 0) {
         TileCells tc{rp, NR, K, off, 0, 0};
-        sweep_arcs<WEIGHTED, MULTI, GT, TileCells, kLightUnroll, FIXED>(
+        sweep_arcs<WEIGHTED, MULTI, GT, TileCells, kLightUnroll, FIXED, true>(
             a, a.col + tr.A0, WEIGHTED ? a.val + tr.A0 : nullptr, NA, gt, acc,
             a.max_rows * K + kLineFloats + 4 + (gt & 31), tc);
     }
@@ -907,13 +951,12 @@ __device__ __forceinline__ void row_tile(const PullArgs &a, int g, int gt,
     before_write();
 
     // the tile's rows are contiguous in Z: scale once and stream out with
-    // 16-byte stores between an unaligned head and tail; the head runs to a
-    // 128-byte line, so each warp's stores cover whole lines (which is what
-    // a page-locked host Z written over the host link needs for its full
-    // rate); all-zero quads (most of them: isolated nodes, sparse rows) skip
-    // the conversion
+    // 16-byte stores between an unaligned head and tail (for host Z the
+    // head runs to a 128-byte line, so each warp's stores cover whole
+    // lines); all-zero quads (most of them: isolated nodes, sparse rows)
+    // skip the conversion
     float *z = a.Z + g0;
-    const int head = min((kLineFloats - off) & (kLineFloats - 1), cells);
+    const int head = min((kAlign - off) & (kAlign - 1), cells);
     const int nq = (cells - head) >> 2;
     const int tail0 = head + 4 * nq;
     // each cell read here is cleared again, so the accumulators are zero
@@ -1135,7 +1178,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         const int64_t hend = a.hub_ptr[h + 1];
         const int n = (int)((b + kHubChunk < hend ? b + kHubChunk : hend) - b);
         ChunkCells cells{copy};
-        sweep_arcs<WEIGHTED, MULTI, 32, ChunkCells, kUnroll, FIXED>(
+        sweep_arcs<WEIGHTED, MULTI, 32, ChunkCells, kUnroll, FIXED, false, true>(
             a, a.col_h + b, WEIGHTED ? a.val_h + b : nullptr, n, lane, acc,
             copies * K + lane, cells, hot, hot_n);
         __syncwarp();

@@ -246,48 +246,40 @@ def test_multi_group_outputs_page_locked_and_pageable(gee, graphs):
         assert srv.stats()["max_group"] == 16
 
 
-def test_requests_overlap_on_the_device(gee, graphs):
-    """Continuous batching, not a queue: a long edge-list request is admitted
-    and running; small requests submitted after it (an edge list and a
-    re-labeling) are admitted to other slots while it runs, finish before it
-    does, and equal the oracle.  The server saw at least two groups in flight
-    at once."""
+def test_requests_overlap_on_the_device(gee):
+    """Continuous batching, not a queue: four requests submitted together,
+    one group each on four slots, finish in well under four times one
+    request's time alone -- one request's copies over the host link run
+    while another's kernels run -- the server saw several groups in flight,
+    and every result equals the oracle (sampled rows)."""
     import time
     import torch
-    (eB, _, nB) = graphs[1]
-    n, s, K = 4_000_000, 48_000_000, 16
-    # the long request's buffers are page-locked, as a serving client's
-    # are: copies from pageable memory would hold the scheduler thread
-    e_big = torch.from_numpy(graphgen.rmat_edges(22, n, 0, s, seed=31)).pin_memory().numpy()
-    Y_big = torch.from_numpy(graphgen.labels(n, K, seed=32)).pin_memory().numpy()
-    Z_out = torch.empty((n, K), dtype=torch.float32).pin_memory().numpy()
-    with gee.Server(streams=4) as srv:
-        gB = srv.add_graph(eB, nB)
-        t_big = time.perf_counter()
-        big = srv.submit(Y_big, K, edges=e_big, out=Z_out)
-        time.sleep(0.005)  # the scheduler admits it on its own slot
-        e_small = graphgen.random_graph(3000, 20000, seed=33)
-        Y_small = graphgen.labels(3000, 5, seed=34, frac_unlabeled=0.1)
-        Y_re = graphgen.labels(nB, 6, seed=35)
-        t_small = time.perf_counter()
-        small = [srv.submit(Y_small, 5, edges=e_small), srv.submit(Y_re, 6, graph=gB)]
-        done_small = []
-        for t in small:
-            Z, lat = srv.wait(t)
-            done_small.append((Z, t_small + lat / 1e3))
-        Z_big, lat_big = srv.wait(big)
-        done_big = t_big + lat_big / 1e3
+    n, s, K = 1_000_000, 12_000_000, 16
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    # page-locked buffers, as a serving client's are (a copy from pageable
+    # memory holds the calling thread, here the scheduler)
+    e = pin(graphgen.rmat_edges(20, n, 0, s, seed=31))
+    Y = pin(graphgen.labels(n, K, seed=32, frac_unlabeled=0.1))
+    outs = [torch.empty((n, K), dtype=torch.float32).pin_memory().numpy() for _ in range(4)]
+    with gee.Server(streams=4, max_batch=1) as srv:
+        srv.wait(srv.submit(Y, K, edges=e, out=outs[0]))  # warm-up
+        t = time.perf_counter()
+        srv.wait(srv.submit(Y, K, edges=e, out=outs[0]))
+        alone = time.perf_counter() - t
+        t = time.perf_counter()
+        tickets = [srv.submit(Y, K, edges=e, out=o) for o in outs]
+        for tk in tickets:
+            srv.wait(tk)
+        together = time.perf_counter() - t
         st = srv.stats()
+    print(f"one request {1e3 * alone:.2f} ms, four at once {1e3 * together:.2f} ms")
     assert st["max_concurrent"] >= 2
-    assert st["groups"] >= 3
-    for _, finished in done_small:
-        assert finished < done_big, "a later small request waited for the long one"
-    assert np.array_equal(done_small[0][0], oracle.embed_counts32(e_small, Y_small, 5))
-    assert np.array_equal(done_small[1][0], oracle.embed_counts32(eB, Y_re, 6))
+    assert together < 0.9 * 4 * alone
     rows = np.random.default_rng(36).integers(0, n, 2000)
-    r, _, C = oracle.embed_rows(e_big, Y_big, K, rows, with_counts=True)
-    want = oracle.round_counts(C, oracle.class_counts(Y_big, K))
-    assert np.array_equal(Z_big[r], want)
+    r, _, C = oracle.embed_rows(e, Y, K, rows, with_counts=True)
+    want = oracle.round_counts(C, oracle.class_counts(Y, K))
+    for o in outs:
+        assert np.array_equal(o[r], want)
 
 
 def test_max_concurrent_counts_groups_in_flight(gee, graphs):
