@@ -15,7 +15,10 @@ the dominant kernel (k_pull) from CUDA events recorded live on its stream;
 `e2e` the same metric through the host-buffer entry point with the label
 upload and the Z download inside the timed region; `cpu_baseline` the FP64
 oracle on a bounded sample; `oneshot` the edge-list entry point (gee_embed)
-that builds nothing resident.
+that builds nothing resident; `serving` (one GPU) the metric's second half:
+1,000 requests of the serving workload through the request loop
+(gee_server_*), p50/p99 latency and edges/s beside one-at-a-time plain
+calls.
 
 `--impl reference` times the oracle (serial C, FP64) on the host cores
 instead, on bounded samples of the same workload.
@@ -209,6 +212,33 @@ def max_over_ranks(x, world):
     t = torch.tensor([float(x)], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+# Random one-byte label gathers that miss L1 cost about one SM clock each in
+# the L1 unit: 0.94 per SM clock on any number of SMs and for every load
+# form (microbenchmark of random byte loads over a 65.6 MB L2-resident
+# array; profiles/k_pull_paper_shift3_full.md).
+GATHERS_PER_SM_CLOCK = 0.94
+
+
+def gather_bound(g, prof, clocks):
+    """The hub-row kernel's second bound: its label gathers that do not come
+    from its shared-memory copy, at GATHERS_PER_SM_CLOCK per SM clock on
+    every SM, against its measured average launch time."""
+    import torch
+    if "k_pull_heavy" not in prof:
+        return None
+    ga = g.gathers()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    bound_ms = ga["hub_other"] / (GATHERS_PER_SM_CLOCK * sms * mhz * 1e6) * 1e3
+    heavy_ms = prof["k_pull_heavy"]["total_ms"] / max(1, prof["k_pull_heavy"]["launches"])
+    return {"kernel": "k_pull_heavy", "bound": "L1 label gathers",
+            "gathers_per_launch": ga["hub_other"],
+            "shared_memory_labels_per_launch": ga["hub_shared"],
+            "rate_per_sm_clock": GATHERS_PER_SM_CLOCK, "sms": sms, "sm_mhz": mhz,
+            "bound_ms": bound_ms, "avg_launch_ms": heavy_ms,
+            "frac": bound_ms / heavy_ms}
 
 
 def algorithmic_bytes(w):
@@ -573,13 +603,14 @@ def _host_link_rates(dev, nbytes=1 << 30, reps=3):
             "both_gbs": timed(True, True), "probe_bytes": nbytes}
 
 
-def run_serve(args, w, world, rank, local):
-    """Serving (gee_server_*): a burst of all requests for the server's
-    throughput, then a Poisson stream at `load` x the plain path's capacity
-    for its latencies; the plain path is one synchronous host-buffer call per
-    request (gee_embed_host, or gee_embed_graph_host on a resident graph),
-    whose latencies under the same arrivals follow from its measured service
-    times (first-in first-out, one call at a time)."""
+def serve_measure(args, w, local, R):
+    """Serving (gee_server_*) on R requests: a burst of all requests for the
+    server's throughput, then a Poisson stream at `load` x the plain path's
+    capacity for its latencies; the plain path is one synchronous host-buffer
+    call per request (gee_embed_host, or gee_embed_graph_host on a resident
+    graph), whose latencies under the same arrivals follow from its measured
+    service times (first-in first-out, one call at a time).  Returns the
+    figures as a dict."""
     import threading
 
     import numpy as np
@@ -592,7 +623,7 @@ def run_serve(args, w, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rng = np.random.default_rng(w["seed"])
-    P, R = w["pool"], args.requests
+    P = w["pool"]
     # the graph pool: edges and four label vectors per graph in pinned memory
     pool = []
     for g in range(P):
@@ -723,17 +754,12 @@ def run_serve(args, w, world, rank, local):
     link = _host_link_rates(dev)
     floor_s = max(h2d / (link["h2d_gbs"] * 1e9), d2h / (link["d2h_gbs"] * 1e9),
                   (h2d + d2h) / (link["both_gbs"] * 1e9))
-    line = {
-        "metric": "serving: edges/s and p50/p99 latency vs sequential plain calls",
-        "value": world * total_edges / burst_s, "unit": "edges/s", "n_gpus": world,
-        "steps": R, "warmup": 2, "ms_per_step": burst_s * 1e3 / R,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w["desc"], "name": args.workload, "requests": R,
+    return {
+        "requests": R, "total_edges": total_edges, "burst_s": burst_s,
+        "config": {"workload": w["desc"], "requests": R,
                    "pool_graphs": P, "resident_graphs": len(resident),
                    "edges_total": total_edges, "budget_bytes": w["budget"],
-                   "streams": w["streams"], "max_batch": w["max_batch"],
-                   "parallelism": "replicas"},
+                   "streams": w["streams"], "max_batch": w["max_batch"]},
         "plain": {"value": total_edges / plain_total, "seconds": plain_total,
                   "p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99),
                   "api": "gee_embed_host / gee_embed_graph_host, one at a time"},
@@ -743,13 +769,36 @@ def run_serve(args, w, world, rank, local):
                    "p50_ms_plain_same_arrivals": pct(plain_lat, 50),
                    "p99_ms_plain_same_arrivals": pct(plain_lat, 99)},
         "speedup_vs_plain": plain_total / burst_s,
-        "e2e": {"value": world * total_edges / burst_s, "unit": "edges/s",
-                "h2d_bytes_per_step": h2d / R, "d2h_bytes_per_step": d2h / R},
+        "h2d_bytes": h2d, "d2h_bytes": d2h,
         "host_link": dict(link, h2d_bytes=h2d, d2h_bytes=d2h, floor_seconds=floor_s,
                           burst_frac_of_floor=floor_s / burst_s),
         "max_abs_diff_vs_plain": worst,
         "server_stats": {"burst": st_burst, "end": st},
         "clocks": clocks,
+    }
+
+
+def run_serve(args, w, world, rank, local):
+    """The serving workload's own JSON line (serve_measure on
+    --requests requests)."""
+    m = serve_measure(args, w, local, args.requests)
+    R, total_edges, burst_s = m["requests"], m["total_edges"], m["burst_s"]
+    line = {
+        "metric": "serving: edges/s and p50/p99 latency vs sequential plain calls",
+        "value": world * total_edges / burst_s, "unit": "edges/s", "n_gpus": world,
+        "steps": R, "warmup": 2, "ms_per_step": burst_s * 1e3 / R,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": dict(m["config"], name=args.workload, parallelism="replicas"),
+        "plain": m["plain"], "served": m["served"],
+        "speedup_vs_plain": m["speedup_vs_plain"],
+        "e2e": {"value": world * total_edges / burst_s, "unit": "edges/s",
+                "h2d_bytes_per_step": m["h2d_bytes"] / R,
+                "d2h_bytes_per_step": m["d2h_bytes"] / R},
+        "host_link": m["host_link"],
+        "max_abs_diff_vs_plain": m["max_abs_diff_vs_plain"],
+        "server_stats": m["server_stats"],
+        "clocks": m["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1025,7 +1074,8 @@ def run_ours(args, w, world, rank, local):
                      # the looser reading: also two 4-byte label gathers per edge
                      "loose_bytes_per_step": algorithmic_bytes(w) + 8 * s,
                      "loose_frac": (algorithmic_bytes(w) + 8 * s)
-                     / (ms_per_step * 1e-3) / 1e9 / peak},
+                     / (ms_per_step * 1e-3) / 1e9 / peak,
+                     "gather_bound": gather_bound(g, prof, clocks)},
         "kernels": {k: dict({"launches": v["launches"],
                              "avg_ms": v["total_ms"] / max(1, v["launches"])},
                             **({"gbs": kernel_bytes[k] / (v["total_ms"] / max(1, v["launches"]))
@@ -1098,6 +1148,33 @@ def run_ours(args, w, world, rank, local):
 
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, True, shift=args.cpu_shift)
+    if (args.workload == "paper" and world == 1 and args.serve_requests > 0
+            and not args.no_serve):
+        # the metric's second half: serving p50/p99 beside plain calls, on
+        # the serving workload's request mix (the paper graph freed first)
+        del edges, Y, Z, wts
+        torch.cuda.empty_cache()
+        ws = dict(WORKLOADS["serve"])
+        if args.serve_streams:
+            ws["streams"] = args.serve_streams
+        if args.serve_batch:
+            ws["max_batch"] = args.serve_batch
+        m = serve_measure(args, ws, local, args.serve_requests)
+        result["serving"] = {
+            "requests": m["requests"], "workload": ws["desc"],
+            "edges_per_s": m["served"]["edges_per_s"],
+            "plain_edges_per_s": m["plain"]["value"],
+            "speedup_vs_plain": m["speedup_vs_plain"],
+            "p50_ms": m["served"]["p50_ms"], "p99_ms": m["served"]["p99_ms"],
+            "plain_p50_ms": m["served"]["p50_ms_plain_same_arrivals"],
+            "plain_p99_ms": m["served"]["p99_ms_plain_same_arrivals"],
+            "load_vs_plain_capacity": m["served"]["load_vs_plain_capacity"],
+            "host_link": {k: m["host_link"][k] for k in
+                          ("h2d_gbs", "d2h_gbs", "both_gbs", "floor_seconds",
+                           "burst_frac_of_floor")},
+            "max_concurrent_groups": m["server_stats"]["end"]["max_concurrent"],
+            "max_abs_diff_vs_plain": m["max_abs_diff_vs_plain"],
+        }
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -1123,6 +1200,10 @@ def main():
                     help="serve workload: requests per group (0: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oneshot", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="paper workload: skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="paper workload: requests of the serving measurement")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     args = ap.parse_args()

@@ -1051,6 +1051,33 @@ gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
     return GEE_OK;
 }
 
+gee_status gee_graph_gathers(const gee_graph *graph, int64_t *hub_shared,
+                             int64_t *hub_other, int64_t *light,
+                             gee_stream_t stream_)
+{
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (graph == nullptr)
+        return GEE_ERR_INVALID_ARG;
+    const Csr &c = graph->csr;
+    unsigned long long hs = 0ull;
+    {
+        Workspace ws(stream);
+        unsigned long long *d = nullptr;
+        GEE_CHECK_CUDA(ws.alloc((void **)&d, sizeof(unsigned long long)));
+        GEE_CHECK_CUDA(count_hub_shared_arcs(c, d, stream));
+        GEE_CHECK_CUDA(cudaMemcpyAsync(&hs, d, sizeof(hs),
+                                       cudaMemcpyDeviceToHost, stream));
+        GEE_CHECK_CUDA(cudaStreamSynchronize(stream));
+    }
+    if (hub_shared)
+        *hub_shared = (int64_t)hs;
+    if (hub_other)
+        *hub_other = c.hub_arcs - (int64_t)hs;
+    if (light)
+        *light = c.nnz_main;
+    return GEE_OK;
+}
+
 gee_status gee_embed_graph(gee_graph *graph, const int32_t *Y, int32_t K,
                            int32_t laplacian, float *Z,
                            const gee_options *opts, gee_stream_t stream_)

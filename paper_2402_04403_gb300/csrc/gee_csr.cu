@@ -1444,6 +1444,37 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
 #undef GEE_TRY
 }
 
+namespace {
+
+// Arcs [0, m) of col whose target rank is below `below`.
+__global__ void k_count_below(const int32_t *__restrict__ col, int64_t m,
+                              int32_t below, unsigned long long *out)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0ull;
+    for (int64_t i = tid; i < m; i += nth)
+        c += col[i] < below ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1)
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c != 0ull)
+        atomicAdd(out, c);
+}
+
+}  // namespace
+
+cudaError_t count_hub_shared_arcs(const Csr &g, unsigned long long *d_out,
+                                  cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess || g.hub_arcs == 0)
+        return e;
+    const int32_t hot = (int32_t)(min((int64_t)kHotLabels, g.n) & ~int64_t(15));
+    k_count_below<<<grid_for(g.hub_arcs, 256, sm_count() * 8), 256, 0, stream>>>(
+        g.col_h, g.hub_arcs, hot, d_out);
+    return cudaGetLastError();
+}
+
 cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
                                    cudaStream_t stream)
 {

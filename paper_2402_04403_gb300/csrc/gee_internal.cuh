@@ -283,6 +283,11 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
                       Allocator &persist, Allocator &tmp, Csr &g,
                       DevStatus *st, cudaStream_t stream);
 
+// Hub-row arcs whose target's label the hub kernel takes from its
+// shared-memory copy (*d_out, device, one counter).
+cudaError_t count_hub_shared_arcs(const Csr &g, unsigned long long *d_out,
+                                  cudaStream_t stream);
+
 // Laplacian arc values w / sqrt(d_u d_v) from the CSR's row sums.
 cudaError_t build_laplacian_values(Csr &g, Allocator &persist, Allocator &tmp,
                                    cudaStream_t stream);

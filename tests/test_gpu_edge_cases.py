@@ -136,3 +136,16 @@ def test_unsupervised_on_degenerate_graphs(gee):
                 _check_choice(edges, Y, K, got)
                 assert np.array_equal(Z.cpu().numpy(), oracle.embed_counts32(edges, got, K)), name
                 Y = got
+
+
+def test_graph_gathers_partition_the_arcs(gee):
+    """gee_graph_gathers: the hub rows' arcs split into labels from the
+    shared-memory copy and the rest; with the light rows' arcs they are
+    every arc (two per edge)."""
+    n, s = 300_000, 3_000_000
+    edges = graphgen.rmat_edges(19, n, 0, s, seed=12)
+    with gee.Graph(_dev(edges), n) as g:
+        info, ga = g.info(), g.gathers()
+    assert ga["hub_shared"] + ga["hub_other"] == info["hub_arcs"]
+    assert ga["hub_shared"] + ga["hub_other"] + ga["light"] == 2 * s
+    assert ga["hub_shared"] > 0 and ga["hub_other"] >= 0
