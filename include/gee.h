@@ -340,7 +340,17 @@ GEE_API gee_status gee_tune_set(const gee_tune_cell *cells, int32_t count);
  * reported, and that problem's Z is undefined); the other problems are
  * still computed.  Returns GEE_OK when every problem succeeded, else the
  * status of the first failing problem (argument errors are found on the
- * host before anything runs).  opts->strategy and opts->block are ignored.
+ * host before anything runs).
+ *
+ * Edge pass: with opts->strategy GEE_BINNED, or GEE_AUTO when most of the
+ * batch's Z cells belong to problems of more than 2^24 cells each (smaller
+ * Z stay in L2 while pushed atomics land), the updates of all problems go through
+ * one binned sequence (records grouped by row tile, each tile summed in
+ * shared memory; float sums with their rounding errors kept beside them,
+ * and if any problem has weights every problem is summed in float, which
+ * is exact for counts below 2^24); endpoints are then always checked
+ * before Z is written, whatever validate_edges says.  Otherwise updates
+ * are pushed into Z with red.global atomics.  opts->block is ignored.
  */
 typedef struct gee_problem {
     const int32_t *edges;    /* int32 [s][2], 8-byte aligned */

@@ -135,7 +135,7 @@ def embed(edges, Y, K: int, weights=None, laplacian: bool = False, *,
     return out
 
 
-def embed_batch(problems, *, validate_edges: bool = True, stream=None,
+def embed_batch(problems, *, validate_edges: bool = True, strategy="auto", stream=None,
                 raise_on_error: bool = True):
     """gee_embed_batch: many independent problems in one launch sequence.
 
@@ -163,7 +163,7 @@ def embed_batch(problems, *, validate_edges: bool = True, stream=None,
         arr[i].reserved = 0
         arr[i].Z = _dev_ptr(out, torch.float32, "out", (n, K))
     statuses = (ctypes.c_int * max(len(problems), 1))()
-    o = options(validate_edges=validate_edges)
+    o = options(strategy, validate_edges=validate_edges)
     rc = lib().gee_embed_batch(arr, len(problems), statuses, ctypes.byref(o),
                                _stream_handle(stream))
     codes = [int(statuses[i]) for i in range(len(problems))]

@@ -924,7 +924,7 @@ gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
         if (rc == GEE_OK && q.s > 0 && q.n == 0)
             rc = GEE_ERR_NODE_RANGE;
         if (rc == GEE_OK && o.deterministic && q.weights != nullptr)
-            rc = GEE_ERR_UNSUPPORTED;  // batches add floats in global atomics
+            rc = GEE_ERR_UNSUPPORTED;  // float sums in scheduling order
         if (rc != GEE_OK) {
             if (statuses != nullptr)
                 statuses[i] = rc;
@@ -966,7 +966,26 @@ gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
                                    stream));
     GEE_CHECK_CUDA(cudaMemcpyAsync(dP, P.data(), sizeof(BatchProblem) * count,
                                    cudaMemcpyHostToDevice, stream));
-    GEE_CHECK_CUDA(batch_enqueue(dh, dP, hh, o.validate_edges != 0, stream));
+    // the edge pass: binned (records grouped by row tile, no atomics on Z)
+    // when most of the batch's cells belong to problems whose Z is beyond
+    // 2^24 cells, else pushed into Z with atomics -- problems taken in
+    // order keep a small Z in L2 while its atomics land (4,096 graphs of
+    // 1e3-1e5 nodes: 39.6 ms pushed, 60.0 ms binned)
+    int64_t cells = 0, big = 0;
+    for (const BatchProblem &p : P) {
+        cells += p.n * (int64_t)p.K;
+        if (p.n * (int64_t)p.K > kBinnedMinCells)
+            big += p.n * (int64_t)p.K;
+    }
+    const bool binned =
+        (o.strategy == GEE_BINNED || (o.strategy == GEE_AUTO && 2 * big > cells)) &&
+        binned_batch_tiles(P.data(), count) > 0;
+    if (binned) {
+        GEE_CHECK_CUDA(batch_labels_enqueue(dh, dP, stream));
+        GEE_CHECK_CUDA(launch_binned_batch(ws, P.data(), count, stream));
+    } else {
+        GEE_CHECK_CUDA(batch_enqueue(dh, dP, hh, o.validate_edges != 0, stream));
+    }
     std::vector<DevStatus> hs((size_t)count);
     GEE_CHECK_CUDA(cudaMemcpyAsync(hs.data(), st, sizeof(DevStatus) * count,
                                    cudaMemcpyDeviceToHost, stream));

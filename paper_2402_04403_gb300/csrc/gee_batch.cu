@@ -329,6 +329,21 @@ cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
     return cudaGetLastError();
 }
 
+cudaError_t batch_labels_enqueue(BatchHeader *dh, const BatchProblem *dP,
+                                 cudaStream_t stream)
+{
+    const int sms = sm_count();
+    {
+        ProfScope p("k_batch_init", stream);
+        k_batch_init<<<sms * 4, 256, 0, stream>>>(dh, dP);
+    }
+    {
+        ProfScope p("k_batch_labels", stream);
+        k_batch_labels<<<2 * sms, kBatchThreads, 0, stream>>>(dh, dP);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
                                bool validate, cudaStream_t stream,
                                cudaGraphExec_t *exec)

@@ -1032,4 +1032,68 @@ cudaError_t launch_binned(Allocator &al, const int32_t *E, const float *w,
     return bin_enqueue(al, pl, dP, weighted, r != nullptr, stream);
 }
 
+int64_t binned_batch_tiles(const BatchProblem *P, int count)
+{
+    bool weighted = false;
+    for (int i = 0; i < count; ++i)
+        weighted |= P[i].w != nullptr;
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t rows = bin_rows(P[i].K, weighted);
+        tiles += (P[i].n + rows - 1) / rows;
+    }
+    int32_t coarse = 0, group = 0;
+    return bin_layout(tiles, &coarse, &group) ? tiles : 0;
+}
+
+cudaError_t launch_binned_batch(Allocator &al, const BatchProblem *P,
+                                int count, cudaStream_t stream)
+{
+    bool weighted = false;
+    for (int i = 0; i < count; ++i)
+        weighted |= P[i].w != nullptr;
+    std::vector<BinProblem> hp((size_t)count);
+    int64_t tiles = 0, chunks = 0, records = 0;
+    for (int i = 0; i < count; ++i) {
+        const BatchProblem &q = P[i];
+        BinProblem &b = hp[(size_t)i];
+        b = BinProblem{};
+        b.E = q.E;
+        b.w = q.w;
+        b.s = q.s;
+        b.n = q.n;
+        b.Yc = q.Yc;
+        b.r = nullptr;
+        b.Z = q.Z;
+        b.counts = q.counts;
+        b.st = q.st;
+        b.K = q.K;
+        b.rows = bin_rows(q.K, weighted);
+        b.row_shift = (uint32_t)__builtin_ctz((unsigned)b.rows);
+        b.kmagic = q.K > 1 ? (uint32_t)(0xFFFFFFFFull / (uint32_t)q.K + 1ull) : 0u;
+        b.tile0 = tiles;
+        b.tiles = (q.n + b.rows - 1) / b.rows;
+        b.chunk0 = chunks;
+        tiles += b.tiles;
+        chunks += (q.s + kEdgeChunk - 1) / kEdgeChunk;
+        records += 2 * q.s;
+    }
+    BinPlan pl{};
+    pl.problems = count;
+    pl.tiles = tiles;
+    pl.edge_chunks = chunks;
+    pl.records = records;
+    if (count < 1 || !bin_layout(tiles, &pl.coarse, &pl.group))
+        return cudaErrorInvalidValue;
+    pl.group_shift = (uint32_t)__builtin_ctz((unsigned)pl.group);
+    BinProblem *dP = nullptr;
+    cudaError_t e = al.alloc((void **)&dP, sizeof(BinProblem) * count);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dP, hp.data(), sizeof(BinProblem) * count,
+                            cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess)
+        return e;
+    return bin_enqueue(al, pl, dP, weighted, false, stream);
+}
+
 }  // namespace gee

@@ -399,6 +399,10 @@ int64_t batch_layout(BatchProblem *P, int count, BatchHeader &h);
 cudaError_t batch_enqueue(BatchHeader *dh, const BatchProblem *dP,
                           const BatchHeader &hh, bool validate,
                           cudaStream_t stream);
+// Only the first two phases (status words and class counts zeroed, labels
+// checked, compacted and counted), for a batch whose edge pass runs binned.
+cudaError_t batch_labels_enqueue(BatchHeader *dh, const BatchProblem *dP,
+                                 cudaStream_t stream);
 // ... into an executable CUDA graph and replayed for every batch whose
 // header and table are written to the same dh and dP.
 cudaError_t batch_graph_create(BatchHeader *dh, const BatchProblem *dP,
@@ -453,6 +457,14 @@ size_t bin_scratch_bytes(int64_t records, int64_t tiles, bool weighted);
 // memory; pl's sizes set by the caller, its arrays allocated here.
 cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
                         bool weighted, bool laplacian, cudaStream_t stream);
+// S4 + S5 of a batch's problems in one binned sequence (problems in the
+// host table P with their device Yc, counts and status set; labels done).
+// Float sums for all problems if any has weights (unit weights then sum
+// exactly).  cudaErrorInvalidValue if the tiles exceed the layout.
+cudaError_t launch_binned_batch(Allocator &al, const BatchProblem *P,
+                                int count, cudaStream_t stream);
+// Row tiles of a batch's binned sequence (0 beyond the layout's limit).
+int64_t binned_batch_tiles(const BatchProblem *P, int count);
 // S4 + S5 of one edge list: endpoints checked (GEE_ERR_NODE_RANGE before Z
 // is written), Z written in full.  Yc, counts (and r) from S1-S3.
 cudaError_t launch_binned(Allocator &al, const int32_t *E, const float *w,

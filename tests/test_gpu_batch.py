@@ -68,11 +68,13 @@ def _mixed_problems(count, seed):
     return out
 
 
-def test_mixed_batch_matches_oracle(gee):
+@pytest.mark.parametrize("strategy", ["atomic", "binned"])
+def test_mixed_batch_matches_oracle(gee, strategy):
+    """Both edge passes of a batch: pushed atomics and binned records."""
     probs = _mixed_problems(60, seed=1)
     dev = [dict(edges=_dev(e), Y=_dev(Y), K=K, weights=None if w is None else _dev(w))
            for e, Y, K, w in probs]
-    Zs = gee.embed_batch(dev)
+    Zs = gee.embed_batch(dev, strategy=strategy)
     for i, ((e, Y, K, w), Z) in enumerate(zip(probs, Zs)):
         got = Z.cpu().numpy()
         if w is None:
@@ -81,20 +83,22 @@ def test_mixed_batch_matches_oracle(gee):
             _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
 
 
-def test_batch_equals_single_calls(gee):
+@pytest.mark.parametrize("strategy", ["atomic", "binned"])
+def test_batch_equals_single_calls(gee, strategy):
     """Unit weights: the batch gives the same bits as one gee_embed call per
     problem; a second run of the batch gives them again."""
     probs = [p for p in _mixed_problems(40, seed=2) if p[3] is None]
     dev = [dict(edges=_dev(e), Y=_dev(Y), K=K) for e, Y, K, _ in probs]
-    Zs = [Z.cpu().numpy() for Z in gee.embed_batch(dev)]
-    again = [Z.cpu().numpy() for Z in gee.embed_batch(dev)]
+    Zs = [Z.cpu().numpy() for Z in gee.embed_batch(dev, strategy=strategy)]
+    again = [Z.cpu().numpy() for Z in gee.embed_batch(dev, strategy=strategy)]
     for q, Z, Z2 in zip(dev, Zs, again):
         single = gee.embed(q["edges"], q["Y"], q["K"], strategy="atomic").cpu().numpy()
         assert np.array_equal(Z, single)
         assert np.array_equal(Z, Z2)
 
 
-def test_large_and_tiny_problems_in_one_batch(gee):
+@pytest.mark.parametrize("strategy", ["atomic", "binned"])
+def test_large_and_tiny_problems_in_one_batch(gee, strategy):
     """A problem spanning many chunks of every kind between tiny ones."""
     n, s, K = 150_000, 1_500_000, 13
     big = (graphgen.rmat_edges(18, n, 0, s, seed=5),
@@ -102,12 +106,14 @@ def test_large_and_tiny_problems_in_one_batch(gee):
     tiny = [(graphgen.random_graph(7, 11, seed=i), graphgen.labels(7, 3, seed=i), 3)
             for i in range(5)]
     probs = tiny[:2] + [big] + tiny[2:]
-    Zs = gee.embed_batch([dict(edges=_dev(e), Y=_dev(Y), K=K) for e, Y, K in probs])
+    Zs = gee.embed_batch([dict(edges=_dev(e), Y=_dev(Y), K=K) for e, Y, K in probs],
+                         strategy=strategy)
     for (e, Y, K), Z in zip(probs, Zs):
         assert np.array_equal(Z.cpu().numpy(), oracle.embed_counts32(e, Y, K))
 
 
-def test_failing_problems_leave_the_rest_intact(gee):
+@pytest.mark.parametrize("strategy", ["atomic", "binned"])
+def test_failing_problems_leave_the_rest_intact(gee, strategy):
     import torch
     probs = _mixed_problems(8, seed=3)
     dev = []
@@ -119,7 +125,7 @@ def test_failing_problems_leave_the_rest_intact(gee):
     dev[bad_label]["Y"][0] = dev[bad_label]["K"]          # label == K
     assert probs[bad_node][0].shape[0] > 0
     dev[bad_node]["edges"][0, 1] = probs[bad_node][1].size  # endpoint == n
-    Zs, codes = gee.embed_batch(dev, raise_on_error=False)
+    Zs, codes = gee.embed_batch(dev, strategy=strategy, raise_on_error=False)
     names = [gee.STATUS_NAMES[c] for c in codes]
     assert names[bad_label] == "GEE_ERR_LABEL_RANGE"
     assert names[bad_node] == "GEE_ERR_NODE_RANGE"
@@ -134,7 +140,7 @@ def test_failing_problems_leave_the_rest_intact(gee):
         else:
             _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
     with pytest.raises(gee.GeeError) as ei:
-        gee.embed_batch(dev)
+        gee.embed_batch(dev, strategy=strategy)
     assert ei.value.name == "GEE_ERR_LABEL_RANGE"
 
 
@@ -150,3 +156,28 @@ def test_empty_batch_and_argument_errors(gee):
     assert gee.STATUS_NAMES[lib.gee_embed_batch(arr, 1, st, None, None)] == \
         "GEE_ERR_INVALID_ARG"
     assert gee.STATUS_NAMES[st[0]] == "GEE_ERR_INVALID_ARG"
+
+
+def test_binned_batch_over_many_tiles(gee):
+    """Enough problems that the binned sequence spans many row tiles and
+    coarse bins, weighted and unit problems mixed (all summed in float),
+    each equal to its oracle result."""
+    rng = np.random.default_rng(9)
+    probs = []
+    for i in range(40):
+        n = int(rng.integers(20_000, 200_000))
+        K = int(rng.integers(2, 60))
+        s = int(n * rng.uniform(2, 10))
+        e = graphgen.rmat_edges(int(np.ceil(np.log2(n))), n, 0, s, seed=700 + i)
+        Y = graphgen.labels(n, K, seed=800 + i, frac_unlabeled=0.1)
+        w = graphgen.weights(s, seed=900 + i) if i % 3 == 0 else None
+        probs.append((e, Y, K, w))
+    dev = [dict(edges=_dev(e), Y=_dev(Y), K=K, weights=None if w is None else _dev(w))
+           for e, Y, K, w in probs]
+    Zs = gee.embed_batch(dev, strategy="binned")
+    for i, ((e, Y, K, w), Z) in enumerate(zip(probs, Zs)):
+        got = Z.cpu().numpy()
+        if w is None:
+            assert np.array_equal(got, oracle.embed_counts32(e, Y, K)), i
+        else:
+            _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
