@@ -907,7 +907,23 @@ def run_precision(args, w, world, rank, local):
         sampled("R-MAT scale 24, weights (0,1], L=32", e_h, w_h, Ys, K, g, n, multi=True)
     with gee.Graph(ed, n) as g:
         sampled("R-MAT scale 24, unit weights", e_h, None, Y_h, K, g, n)
-    del ed, wd, Yd
+    # the one-shot edge-list call's weighted forms on the same rows: pushed
+    # float atomics (sums in scheduling order) and binned records (float
+    # sums with their rounding errors kept)
+    deg = np.bincount(e_h.ravel(), minlength=n)
+    rows = np.unique(np.concatenate([np.argsort(deg)[-64:], rng.integers(0, n, w["rows"])]))
+    Z = torch.empty((n, K), dtype=torch.float32, device=dev)
+    for lap in (False, True):
+        r, z64r = oracle.embed_rows(e_h, Y_h, K, rows, weights=w_h, laplacian=lap)
+        for strat in ("atomic", "binned"):
+            gee.embed(ed, Yd, K, weights=wd, laplacian=lap, strategy=strat, out=Z)
+            form = "Laplacian" if lap else "weight sums"
+            path = (f"FP32 {form}, pushed atomics (one-shot ATOMIC)" if strat == "atomic"
+                    else f"FP32 {form} with compensation (one-shot BINNED)")
+            add("R-MAT scale 24, weights (0,1]", path,
+                _errors(Z[torch.from_numpy(r).to(dev)].cpu().numpy(), z64r),
+                rows_checked=int(r.size))
+    del ed, wd, Yd, Z
     torch.cuda.empty_cache()
     # paper scale, unit weights (the headline workload)
     W = WORKLOADS["paper"]
