@@ -380,7 +380,9 @@ GEE_API gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
  * requests run overlaps with them on the GPU:
  *   - consecutive edge-list requests are fused into one gee_embed_batch
  *     launch sequence (up to max_batch requests / max_batch_edges edges),
- *     replayed as one CUDA graph captured per slot;
+ *     replayed as one CUDA graph captured per slot, or run binned when most
+ *     of the group's cells belong to requests beyond 2^24 cells (as
+ *     gee_embed_batch with GEE_AUTO);
  *   - re-labelings of the same resident graph with the same K and variant
  *     waiting anywhere in the queue are fused into one multi-label pass
  *     (W widened to L*K <= GEE_MAX_COLUMNS columns).
@@ -429,7 +431,8 @@ typedef struct gee_server_stats {
     int64_t max_concurrent;    /* most groups in flight at once */
     int64_t resident_bytes;    /* estimated bytes of resident graphs */
     int64_t peak_inflight_bytes;
-    int64_t graph_launches;    /* edge-list groups run as one CUDA graph */
+    int64_t graph_launches;    /* edge-list groups run as one CUDA graph
+                                  (the others ran binned) */
 } gee_server_stats;
 
 /* cfg may be NULL (defaults).  Uses the current CUDA device. */

@@ -129,10 +129,6 @@ gee_status deterministic_strategy(gee_options &o, bool weighted,
     return o.strategy == GEE_SEGMENTED ? GEE_OK : GEE_ERR_UNSUPPORTED;
 }
 
-// Z cells above which GEE_AUTO takes BINNED (the autotuner's grid ends
-// at 2^24 cells).
-constexpr int64_t kBinnedMinCells = int64_t(1) << 24;
-
 bool binned_fits(int64_t n, int32_t K)
 {
     int32_t coarse = 0, group = 0;
@@ -971,14 +967,9 @@ gee_status gee_embed_batch(const gee_problem *problems, int32_t count,
     // 2^24 cells, else pushed into Z with atomics -- problems taken in
     // order keep a small Z in L2 while its atomics land (4,096 graphs of
     // 1e3-1e5 nodes: 39.6 ms pushed, 60.0 ms binned)
-    int64_t cells = 0, big = 0;
-    for (const BatchProblem &p : P) {
-        cells += p.n * (int64_t)p.K;
-        if (p.n * (int64_t)p.K > kBinnedMinCells)
-            big += p.n * (int64_t)p.K;
-    }
     const bool binned =
-        (o.strategy == GEE_BINNED || (o.strategy == GEE_AUTO && 2 * big > cells)) &&
+        (o.strategy == GEE_BINNED ||
+         (o.strategy == GEE_AUTO && batch_prefers_binned(P.data(), count))) &&
         binned_batch_tiles(P.data(), count) > 0;
     if (binned) {
         GEE_CHECK_CUDA(batch_labels_enqueue(dh, dP, stream));

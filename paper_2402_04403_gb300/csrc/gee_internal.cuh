@@ -445,6 +445,24 @@ struct BinPlan {
     float *val2;
 };
 
+// Z cells beyond which pushed updates miss L2: GEE_AUTO takes BINNED for
+// larger edge-list problems (the autotuner's grid ends here).
+constexpr int64_t kBinnedMinCells = int64_t(1) << 24;
+// A batch (or server group) of problems runs binned when most of its cells
+// belong to problems beyond kBinnedMinCells; small problems keep their Z
+// in L2 while pushed atomics land.
+inline bool batch_prefers_binned(const BatchProblem *P, int count)
+{
+    int64_t cells = 0, big = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t c = P[i].n * (int64_t)P[i].K;
+        cells += c;
+        if (c > kBinnedMinCells)
+            big += c;
+    }
+    return 2 * big > cells;
+}
+
 // Rows per tile for K classes: the largest power of two whose cells fit
 // a tile's accumulators (so rows and bins split by shifts); bin_layout is
 // false when `tiles` row tiles exceed the two-level layout (about 10^6

@@ -17,7 +17,10 @@
 // freed stream-ordered behind it, so the thread never waits for the GPU and
 // groups on different slots overlap.  An edge-list group's kernels are one
 // CUDA graph launch: each slot captures the batch sequence once, over its
-// own fixed header and problem table.  Clients only touch the queue.
+// own fixed header and problem table -- except a group whose cells belong
+// mostly to large requests (Z beyond 2^24 cells), which runs the binned
+// sequence instead (its launches are sized by the group).  Clients only
+// touch the queue.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -75,6 +78,7 @@ struct Slot {
     cudaGraphExec_t batch_graph = nullptr;  // the sequence, captured once
     bool busy = false;
     bool multi = false;                // re-label group
+    bool binned = false;               // edge-list group run binned
     int64_t n = 0;                     // rows of the re-label group's graph
     int64_t bytes = 0;
     std::vector<Req *> reqs;
@@ -197,9 +201,17 @@ namespace {
 
 int64_t edge_request_bytes(int64_t s, int64_t n, int32_t K, bool weighted)
 {
-    return align256(s * 8) + (weighted ? align256(s * 4) : 0) +
-           align256(n * 4) + align256(n * (int64_t)K * 4) + align256(n + 16) +
-           align256((int64_t)K * 4) + align256(sizeof(BatchProblem)) + 1024;
+    int64_t b = align256(s * 8) + (weighted ? align256(s * 4) : 0) +
+                align256(n * 4) + align256(n * (int64_t)K * 4) +
+                align256(n + 16) + align256((int64_t)K * 4) +
+                align256(sizeof(BatchProblem)) + 1024;
+    // a large request makes its group run binned: record scratch (the
+    // group's records are at most the sum of its requests')
+    if (n * (int64_t)K > kBinnedMinCells) {
+        const int64_t rows = bin_rows(K, weighted);
+        b += (int64_t)bin_scratch_bytes(2 * s, (n + rows - 1) / rows, weighted);
+    }
+    return b;
 }
 
 int64_t relabel_request_bytes(int64_t n, int32_t K)
@@ -246,7 +258,8 @@ void gee_server::complete(Slot &sl)
         for (Req *q : sl.reqs)
             finish(q, sl.launch_error);
     } else if (!sl.multi) {
-        ++stats.graph_launches;
+        if (!sl.binned)
+            ++stats.graph_launches;
         for (size_t i = 0; i < sl.reqs.size(); ++i)
             finish(sl.reqs[i], static_cast<gee_status>(sl.host_st[i].code));
     } else {
@@ -328,7 +341,17 @@ gee_status gee_server::launch_edges(Slot &sl)
     GEE_CHECK_CUDA_RET(cudaMemcpyAsync(dP, sl.host_tab,
                                        sizeof(BatchProblem) * count,
                                        cudaMemcpyHostToDevice, st));
-    GEE_CHECK_CUDA_RET(cudaGraphLaunch(sl.batch_graph, st));
+    // large requests: labels, then one binned sequence over the group's
+    // row tiles (launches sized by the group, so not the captured graph);
+    // else the slot's captured batch sequence with pushed atomics
+    sl.binned = batch_prefers_binned(sl.host_tab, count) &&
+                binned_batch_tiles(sl.host_tab, count) > 0;
+    if (sl.binned) {
+        GEE_CHECK_CUDA_RET(batch_labels_enqueue(dh, dP, st));
+        GEE_CHECK_CUDA_RET(launch_binned_batch(ws, sl.host_tab, count, st));
+    } else {
+        GEE_CHECK_CUDA_RET(cudaGraphLaunch(sl.batch_graph, st));
+    }
     GEE_CHECK_CUDA_RET(cudaMemcpyAsync(sl.host_st, dst,
                                        sizeof(DevStatus) * count,
                                        cudaMemcpyDeviceToHost, st));
