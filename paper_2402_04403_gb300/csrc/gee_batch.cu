@@ -18,7 +18,15 @@
 //
 // Warps take fixed-size chunks from one counter per phase, in problem
 // order, so the few problems in flight at any time keep their Z in L2 while
-// the atomics land.  A problem whose labels or endpoints fail validation is
+// the atomics land.  The scatter's chunks are small (kBatchEdgeChunk = 1,024
+// edges) because its working set is the Z rows of every chunk in flight,
+// one per warp: 4,096 graphs of 1e3-1e5 nodes took 31.9 ms in the scatter
+// with 4,096-edge chunks, 21.4 ms with 1,024.  Its bound is then the L2's
+// tag lookups (74.7 % busy: two reductions and two label reads per edge);
+// chunks dealt to warps statically (78 ms), drawn from 16 counters (39 ms),
+// whole-CTA spans with the labels in shared memory (60 ms), or one launch
+// that clears, adds and finishes each problem in turn under bounded waits
+// (38.6 ms against 27 ms for the three launches) were all slower.  A problem whose labels or endpoints fail validation is
 // skipped by the later phases and its Z is left untouched.  The launch
 // arguments are only the device addresses of the header and the problem
 // table, so one CUDA graph of the sequence serves every batch that reuses
@@ -32,6 +40,8 @@ namespace {
 constexpr int kBatchThreads = 512;
 constexpr int kUnroll = 4;  // independent elements per lane in flight
 constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int64_t kValidateSpan =
+    kBatchEdgeChunk >= 4096 ? 1 : 4096 / kBatchEdgeChunk;
 
 __device__ __forceinline__ int64_t chunk0_of(const BatchProblem &p, int kind)
 {
@@ -122,12 +132,18 @@ __global__ void __launch_bounds__(kBatchThreads)
     k_batch_validate(BatchHeader *h, const BatchProblem *P)
 {
     const int lane = threadIdx.x & 31;
+    int64_t c = 0, last = 0;  // this warp's next chunk and the end of its draw
     for (;;) {
-        const int64_t c = next_chunk(h, kWorkValidate);
+        if (c == last) {
+            // no locality to keep here: kValidateSpan chunks per draw
+            c = next_chunk(h, kWorkValidate) * kValidateSpan;
+            last = c + kValidateSpan;
+        }
         if (c >= h->edge_chunks)
             break;
         const BatchProblem &p = P[find_problem(P, (int)h->count, kChunkEdges, c)];
-        const int64_t e0 = (c - p.edge_chunk0) * kBatchEdgeChunk;
+        ++c;
+        const int64_t e0 = (c - 1 - p.edge_chunk0) * kBatchEdgeChunk;
         const int64_t e1 = min(e0 + kBatchEdgeChunk, p.s);
         const int2 *E = reinterpret_cast<const int2 *>(p.E);
         for (int64_t b = e0 + lane; b < e1; b += 32 * kUnroll) {

@@ -359,7 +359,7 @@ cudaError_t launch_wide_chunks(const Csr &g, int32_t L, int32_t K,
 // Work is cut into per-warp chunks of each kind; every problem's chunks are
 // numbered consecutively in problem order.
 constexpr int64_t kBatchNodeChunk = 4096;
-constexpr int64_t kBatchEdgeChunk = 4096;
+constexpr int64_t kBatchEdgeChunk = 1024;
 constexpr int64_t kBatchCellChunk = 16384;
 enum { kChunkNodes = 0, kChunkEdges = 1, kChunkCells = 2 };
 enum { kWorkLabels = 0, kWorkValidate, kWorkZero, kWorkScatter, kWorkFinalize,

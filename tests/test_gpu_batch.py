@@ -181,3 +181,29 @@ def test_binned_batch_over_many_tiles(gee):
             assert np.array_equal(got, oracle.embed_counts32(e, Y, K)), i
         else:
             _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
+
+
+def test_many_tiny_problems(gee):
+    """Thousands of problems of a few nodes each (many problems per chunk of
+    work, so their clear, add and finish items interleave closely), each
+    equal to its oracle result."""
+    rng = np.random.default_rng(21)
+    probs = []
+    for i in range(3000):
+        n = int(rng.integers(1, 60))
+        K = int(rng.integers(1, min(n, 8) + 1))
+        s = int(rng.integers(0, 4 * n + 1))
+        e = rng.integers(0, n, size=(s, 2), dtype=np.int32)
+        Y = rng.integers(-1, K, size=n, dtype=np.int32)
+        w = graphgen.weights(s, seed=5000 + i) if i % 2 == 0 and s > 0 else None
+        probs.append((e, Y, K, w))
+    dev = [dict(edges=_dev(e), Y=_dev(Y), K=K, weights=None if w is None else _dev(w))
+           for e, Y, K, w in probs]
+    Zs = gee.embed_batch(dev, strategy="atomic")
+    for i, ((e, Y, K, w), Z) in enumerate(zip(probs, Zs)):
+        got = Z.cpu().numpy()
+        if w is None:
+            assert np.array_equal(got, oracle.embed_counts32(e, Y, K)), i
+        else:
+            _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
+
