@@ -25,6 +25,15 @@
 //                 counts, or float sums with their rounding errors kept
 //                 beside them -- then the tile's rows of Z, written once
 //
+// Up to 65,536 tiles the tile records are laid out by tile pair instead:
+// k_bin_count_pairs counts both endpoints of every edge per pair of tiles
+// (2i, 2i+1) -- 32 K counters, one shared-memory array per CTA -- and each
+// pair gets one region of that size, which tile 2i fills from its start and
+// tile 2i+1 from its end.  The regions' sizes are then known before any
+// record is written, the coarse bins' regions are unions of whole pairs, and
+// k_bin_fine (a read of every coarse record to count them per tile) and its
+// scan drop out.
+//
 // The kernels take a table of problems so that several edge lists can share
 // one sequence of launches; global row tiles number every problem's tiles
 // in problem order.
@@ -219,6 +228,74 @@ __global__ void __launch_bounds__(kEdgeThreads)
     for (int b = threadIdx.x; b < pl.coarse; b += blockDim.x)
         if (hist[b] != 0u)
             atomicAdd(pl.cnt1 + b, (unsigned long long)hist[b]);
+}
+
+// Paired layout: per pair of row tiles, how many updates its rows can
+// receive (both endpoints of every edge), in a shared-memory counter per
+// pair; endpoints outside [0, n) are reported here.  One CTA per SM.
+constexpr int kPairThreads = 1024;
+constexpr int kMaxPairs = 32768;
+
+__global__ void __launch_bounds__(kPairThreads, 1)
+    k_bin_count_pairs(BinPlan pl, const BinProblem *P)
+{
+    extern __shared__ uint32_t pc[];  // [pairs]
+    const int pairs = (int)((pl.tiles + 1) >> 1);
+    for (int i = threadIdx.x; i < pairs; i += blockDim.x)
+        pc[i] = 0u;
+    __syncthreads();
+    constexpr int kPer = kEdgeChunk / kPairThreads;
+    for (int64_t chunk = blockIdx.x; chunk < pl.edge_chunks;
+         chunk += gridDim.x) {
+        const BinProblem &p = P[problem_of_chunk(P, pl.problems, chunk)];
+        const int64_t e0 = (chunk - p.chunk0) * kEdgeChunk;
+        const int64_t e1 = min(e0 + (int64_t)kEdgeChunk, p.s);
+        const int2 *E = reinterpret_cast<const int2 *>(p.E);
+        int2 uv[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t e = e0 + threadIdx.x + (int64_t)j * kPairThreads;
+            uv[j] = e < e1 ? __ldcs(E + e) : make_int2(0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t e = e0 + threadIdx.x + (int64_t)j * kPairThreads;
+            if (e >= e1)
+                continue;
+            if (!node_in(uv[j].x, p.n) || !node_in(uv[j].y, p.n)) {
+                report(p.st, GEE_ERR_NODE_RANGE, (unsigned long long)e);
+                continue;
+            }
+            atomicAdd(pc + (((uint32_t)p.tile0 + ((uint32_t)uv[j].x >> p.row_shift)) >> 1), 1u);
+            atomicAdd(pc + (((uint32_t)p.tile0 + ((uint32_t)uv[j].y >> p.row_shift)) >> 1), 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pairs; i += blockDim.x)
+        if (pc[i] != 0u)
+            atomicAdd(pl.cnt2 + i, (unsigned long long)pc[i]);
+}
+
+// Paired layout: the coarse bins' record offsets from the pairs' (a coarse
+// bin is a run of whole pairs; one bin of one tile when there is one tile).
+__global__ void k_bin_pair_coarse(BinPlan pl)
+{
+    const int64_t pairs = (pl.tiles + 1) >> 1;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= pl.coarse;
+         c += gridDim.x * blockDim.x)
+        pl.off1[c] = pl.off2[min(((int64_t)c * pl.group + 1) >> 1, pairs)];
+}
+
+// First record of tile t's region among the tile records: its pair's
+// region, from the start for an even tile, from the end for an odd one
+// (fill2 holds the records the tile received).
+__device__ __forceinline__ unsigned long long tile_records_start(const BinPlan &pl,
+                                                                 int64_t t)
+{
+    if (!pl.paired)
+        return pl.off2[t];
+    const int64_t q = t >> 1;
+    return (t & 1) ? pl.off2[q + 1] - pl.fill2[t] : pl.off2[q];
 }
 
 // out[i] = sum of x(j) for j < i, i in [0, m]; x(j) = in[j], or with
@@ -576,8 +653,17 @@ __global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
 #pragma unroll
         for (int i = 0; i < kResv; ++i) {
             const int f = threadIdx.x + i * kRecThreads;
-            if (f < G)  // unsigned wrap-around cancels when i is added
-                dst0[f] = pl.off2[(int64_t)c * G + f] + resv[i] - start[f];
+            if (f >= G)
+                continue;
+            // unsigned wrap-around cancels when i is added.  Paired: an even
+            // tile fills its pair's region from the start, an odd one from
+            // the end (this run ends where the tile's previous run began)
+            const int64_t g = (int64_t)c * G + f;
+            const bool odd = pl.paired && (g & 1);
+            const unsigned long long base =
+                pl.off2[pl.paired ? (g >> 1) + (odd ? 1 : 0) : g];
+            dst0[f] = odd ? base - resv[i] - hist[f] - start[f]
+                          : base + resv[i] - start[f];
         }
         __syncthreads();
         const uint32_t total = s_total;
@@ -666,7 +752,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int cells = (int)((r1 - r0) * K);
         float *z = p.Z + r0 * K;
         const int off = (int)((reinterpret_cast<uintptr_t>(z) >> 2) & 3);
-        const unsigned long long rec0 = pl.off2[t];
+        const unsigned long long rec0 = tile_records_start(pl, t);
         const long long nrec = (long long)pl.fill2[t];
         // -- accumulate: keys 8 at a time from a 16-byte boundary
         const uint16_t *k2 = pl.key2 + rec0;
@@ -903,16 +989,41 @@ cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
     auto grid = [&](int64_t work, int per_sm) {
         return (int)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * per_sm));
     };
-    if (pl.edge_chunks > 0) {
-        ProfScope p("k_bin_count", stream);
-        k_bin_count<<<grid(pl.edge_chunks, 4), kEdgeThreads,
-                      (size_t)pl.coarse * 4, stream>>>(pl, dP);
-        if ((e = cudaGetLastError()) != cudaSuccess)
-            return e;
-    }
-    {
-        ProfScope p("k_bin_scan", stream);
-        k_bin_scan<<<1, 1024, 0, stream>>>(pl.cnt1, pl.coarse, 0, pl.off1);
+    // tile records by pair while the pairs' counters fit one CTA's shared
+    // memory (and the coarse keys hold whole tile numbers)
+    const int64_t pairs = (pl.tiles + 1) >> 1;
+    pl.paired = pl.tiles <= 65536 && pairs <= kMaxPairs ? 1 : 0;
+    if (pl.paired) {
+        if (pl.edge_chunks > 0) {
+            ProfScope p("k_bin_count_pairs", stream);
+            const size_t sm_b = (size_t)pairs * 4;
+            if ((e = with_smem(k_bin_count_pairs, sm_b)) != cudaSuccess)
+                return e;
+            k_bin_count_pairs<<<grid(pl.edge_chunks, 1), kPairThreads, sm_b,
+                                stream>>>(pl, dP);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return e;
+        }
+        {
+            ProfScope p("k_bin_scan", stream);
+            k_bin_scan<<<1, 1024, 0, stream>>>(pl.cnt2, pairs, 0, pl.off2);
+        }
+        {
+            ProfScope p("k_bin_pair_coarse", stream);
+            k_bin_pair_coarse<<<(pl.coarse + 256) / 256, 256, 0, stream>>>(pl);
+        }
+    } else {
+        if (pl.edge_chunks > 0) {
+            ProfScope p("k_bin_count", stream);
+            k_bin_count<<<grid(pl.edge_chunks, 4), kEdgeThreads,
+                          (size_t)pl.coarse * 4, stream>>>(pl, dP);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return e;
+        }
+        {
+            ProfScope p("k_bin_scan", stream);
+            k_bin_scan<<<1, 1024, 0, stream>>>(pl.cnt1, pl.coarse, 0, pl.off1);
+        }
     }
     if (pl.edge_chunks > 0) {
         ProfScope p("k_bin_edges", stream);
@@ -943,14 +1054,16 @@ cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
         k_bin_scan<<<1, 1024, 0, stream>>>(pl.fill1, pl.coarse, 1, pl.chunk1);
     }
     const int64_t chunk_bound = pl.records / kRecChunk + pl.coarse;
-    {
-        ProfScope p("k_bin_fine", stream);
-        k_bin_fine<<<grid(chunk_bound, 8), kRecThreads, (size_t)pl.group * 4,
-                     stream>>>(pl);
-    }
-    {
-        ProfScope p("k_bin_scan", stream);
-        k_bin_scan<<<1, 1024, 0, stream>>>(pl.cnt2, (int64_t)fine, 0, pl.off2);
+    if (!pl.paired) {
+        {
+            ProfScope p("k_bin_fine", stream);
+            k_bin_fine<<<grid(chunk_bound, 8), kRecThreads, (size_t)pl.group * 4,
+                         stream>>>(pl);
+        }
+        {
+            ProfScope p("k_bin_scan", stream);
+            k_bin_scan<<<1, 1024, 0, stream>>>(pl.cnt2, (int64_t)fine, 0, pl.off2);
+        }
     }
     {
         ProfScope p("k_bin_split", stream);

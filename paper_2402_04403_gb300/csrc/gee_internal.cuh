@@ -433,7 +433,8 @@ struct BinProblem {
 
 // The launch's sizes and scratch (kernel parameter, by value).
 struct BinPlan {
-    int32_t problems, coarse, group, pad;
+    int32_t problems, coarse, group;
+    int32_t paired;  // tile records laid out by tile pair (see gee_bin.cu)
     int64_t tiles, edge_chunks, records;   // records: capacity (2 s)
     uint32_t group_shift, pad2;             // log2(group): tile -> coarse bin
     unsigned long long *cnt1, *fill1, *off1, *chunk1;  // [coarse + 1]
