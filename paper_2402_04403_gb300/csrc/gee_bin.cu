@@ -46,8 +46,9 @@ namespace {
 constexpr int kEdgeThreads = 512;  // k_bin_count / k_bin_edges
 constexpr int kEdgeChunk = 4096;   // edges per chunk of those kernels
 constexpr int kEdgesPerThread = kEdgeChunk / kEdgeThreads;
-constexpr int kRecThreads = 256;   // k_bin_fine / k_bin_split
-constexpr int kRecChunk = 4096;    // records per chunk of those kernels
+constexpr int kRecThreads = 512;   // k_bin_fine / k_bin_split
+constexpr int kRecChunk = 8192;    // records per chunk of those kernels
+constexpr int kSplitBlocks = 2;    // resident split CTAs per SM (64 registers)
 constexpr int kRecsPerThread = kRecChunk / kRecThreads;
 constexpr int kMaxBins = 1024;     // coarse bins; row tiles per coarse bin
 constexpr int kTileThreads = 1024;
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kRecThreads) k_bin_fine(BinPlan pl)
 
 // Coarse records -> tile records (the low 16 bits), grouped by row tile.
 template <bool WEIGHTED>
-__global__ void __launch_bounds__(kRecThreads, 4) k_bin_split(BinPlan pl)
+__global__ void __launch_bounds__(kRecThreads, kSplitBlocks) k_bin_split(BinPlan pl)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint32_t warp_tot[kRecThreads / 32];
@@ -1072,12 +1073,12 @@ cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
             if ((e = with_smem(k_bin_split<true>, sm_b)) != cudaSuccess)
                 return e;
             k_bin_split<true>
-                <<<grid(chunk_bound, 4), kRecThreads, sm_b, stream>>>(pl);
+                <<<grid(chunk_bound, kSplitBlocks), kRecThreads, sm_b, stream>>>(pl);
         } else {
             if ((e = with_smem(k_bin_split<false>, sm_b)) != cudaSuccess)
                 return e;
             k_bin_split<false>
-                <<<grid(chunk_bound, 4), kRecThreads, sm_b, stream>>>(pl);
+                <<<grid(chunk_bound, kSplitBlocks), kRecThreads, sm_b, stream>>>(pl);
         }
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
