@@ -245,30 +245,49 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     for (int i = threadIdx.x; i < pairs; i += blockDim.x)
         pc[i] = 0u;
     __syncthreads();
+    // two chunks per round, every edge of both loaded before any is
+    // counted (eight loads in flight per thread)
     constexpr int kPer = kEdgeChunk / kPairThreads;
-    for (int64_t chunk = blockIdx.x; chunk < pl.edge_chunks;
-         chunk += gridDim.x) {
-        const BinProblem &p = P[problem_of_chunk(P, pl.problems, chunk)];
-        const int64_t e0 = (chunk - p.chunk0) * kEdgeChunk;
-        const int64_t e1 = min(e0 + (int64_t)kEdgeChunk, p.s);
-        const int2 *E = reinterpret_cast<const int2 *>(p.E);
-        int2 uv[kPer];
+    constexpr int kChunks = 2;
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunks; c0 < pl.edge_chunks;
+         c0 += (int64_t)gridDim.x * kChunks) {
+        const BinProblem *pp[kChunks];
+        int64_t e0[kChunks], e1[kChunks];
+        int2 uv[kChunks][kPer];
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int64_t e = e0 + threadIdx.x + (int64_t)j * kPairThreads;
-            uv[j] = e < e1 ? __ldcs(E + e) : make_int2(0, 0);
+        for (int h = 0; h < kChunks; ++h) {
+            const int64_t chunk = c0 + h;
+            pp[h] = chunk < pl.edge_chunks
+                        ? P + problem_of_chunk(P, pl.problems, chunk)
+                        : P;
+            e0[h] = (chunk - pp[h]->chunk0) * kEdgeChunk;
+            e1[h] = chunk < pl.edge_chunks
+                        ? min(e0[h] + (int64_t)kEdgeChunk, pp[h]->s)
+                        : e0[h];
+            const int2 *E = reinterpret_cast<const int2 *>(pp[h]->E);
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int64_t e = e0[h] + threadIdx.x + (int64_t)j * kPairThreads;
+                uv[h][j] = e < e1[h] ? __ldcs(E + e) : make_int2(0, 0);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int64_t e = e0 + threadIdx.x + (int64_t)j * kPairThreads;
-            if (e >= e1)
-                continue;
-            if (!node_in(uv[j].x, p.n) || !node_in(uv[j].y, p.n)) {
-                report(p.st, GEE_ERR_NODE_RANGE, (unsigned long long)e);
-                continue;
+        for (int h = 0; h < kChunks; ++h) {
+            const BinProblem &p = *pp[h];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int64_t e = e0[h] + threadIdx.x + (int64_t)j * kPairThreads;
+                if (e >= e1[h])
+                    continue;
+                if (!node_in(uv[h][j].x, p.n) || !node_in(uv[h][j].y, p.n)) {
+                    report(p.st, GEE_ERR_NODE_RANGE, (unsigned long long)e);
+                    continue;
+                }
+                atomicAdd(pc + (((uint32_t)p.tile0 +
+                                 ((uint32_t)uv[h][j].x >> p.row_shift)) >> 1), 1u);
+                atomicAdd(pc + (((uint32_t)p.tile0 +
+                                 ((uint32_t)uv[h][j].y >> p.row_shift)) >> 1), 1u);
             }
-            atomicAdd(pc + (((uint32_t)p.tile0 + ((uint32_t)uv[j].x >> p.row_shift)) >> 1), 1u);
-            atomicAdd(pc + (((uint32_t)p.tile0 + ((uint32_t)uv[j].y >> p.row_shift)) >> 1), 1u);
         }
     }
     __syncthreads();
@@ -1000,8 +1019,8 @@ cudaError_t bin_enqueue(Allocator &al, BinPlan &pl, const BinProblem *dP,
             const size_t sm_b = (size_t)pairs * 4;
             if ((e = with_smem(k_bin_count_pairs, sm_b)) != cudaSuccess)
                 return e;
-            k_bin_count_pairs<<<grid(pl.edge_chunks, 1), kPairThreads, sm_b,
-                                stream>>>(pl, dP);
+            k_bin_count_pairs<<<grid((pl.edge_chunks + 1) / 2, 1), kPairThreads,
+                                sm_b, stream>>>(pl, dP);
             if ((e = cudaGetLastError()) != cudaSuccess)
                 return e;
         }
