@@ -254,28 +254,56 @@ __global__ void __launch_bounds__(kBatchThreads)
         const int64_t cells = p.n * p.K;
         const int64_t j0 = (c - p.cell_chunk0) * kBatchCellChunk;
         const int64_t j1 = min(j0 + kBatchCellChunk, cells);
-        // class of cell j0 + lane, then advanced by 32 columns per step
-        int k = (int)((j0 + lane) % p.K);
-        const int dk = 32 % p.K;
+        const int K = p.K;
         uint32_t *C = reinterpret_cast<uint32_t *>(p.Z);
-        for (int64_t b = j0 + lane; b < j1; b += 32 * kUnroll) {
-            uint32_t x[kUnroll];
+        auto value = [&](uint32_t x, int k) {
+            return p.w == nullptr ? count_to_z(x, p.counts[k])
+                                  : sum_to_z(__uint_as_float(x), p.counts[k]);
+        };
+        // 16-byte loads and stores between a scalar head (up to the first
+        // 16-byte boundary of Z) and tail: kUnroll quads per lane in flight
+        const int64_t head =
+            min((int64_t)(((16u - (reinterpret_cast<uintptr_t>(p.Z + j0) & 15u)) &
+                           15u) >> 2),
+                j1 - j0);
+        const int64_t jb = j0 + head;
+        const int64_t nq = (j1 - jb) >> 2;
+        const int64_t jt = jb + 4 * nq;
+        if (lane < head)
+            p.Z[j0 + lane] = value(C[j0 + lane], (int)((j0 + lane) % K));
+        if (lane < j1 - jt)
+            p.Z[jt + lane] = value(C[jt + lane], (int)((jt + lane) % K));
+        const uint4 *C4 = reinterpret_cast<const uint4 *>(C + jb);
+        float4 *Z4 = reinterpret_cast<float4 *>(p.Z + jb);
+        // class of this lane's quad's first cell, advanced by 128 cells per
+        // step
+        int k = (int)((jb + 4 * (int64_t)lane) % K);
+        const int dk = 128 % K;
+        for (int64_t q = lane; q < nq; q += 32 * kUnroll) {
+            uint4 x[kUnroll];
             int kk[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                x[u] = b + 32 * u < j1 ? C[b + 32 * u] : 0u;
+                x[u] = q + 32 * u < nq ? C4[q + 32 * u] : make_uint4(0u, 0u, 0u, 0u);
                 kk[u] = k;
                 k += dk;
-                if (k >= p.K)
-                    k -= p.K;
+                if (k >= K)
+                    k -= K;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-                if (b + 32 * u < j1)
-                    p.Z[b + 32 * u] =
-                        p.w == nullptr
-                            ? count_to_z(x[u], p.counts[kk[u]])
-                            : sum_to_z(__uint_as_float(x[u]), p.counts[kk[u]]);
+                if (q + 32 * u >= nq)
+                    continue;
+                const uint32_t xs[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+                float o[4];
+                int ke = kk[u];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    o[e] = value(xs[e], ke);
+                    if (++ke == K)
+                        ke = 0;
+                }
+                Z4[q + 32 * u] = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
     }
