@@ -221,14 +221,14 @@ def max_over_ranks(x, world):
 GATHERS_PER_SM_CLOCK = 0.94
 
 
-def gather_bound(g, prof, clocks):
+def gather_bound(g, K, prof, clocks):
     """The hub-row kernel's second bound: its label gathers that do not come
-    from its shared-memory copy, at GATHERS_PER_SM_CLOCK per SM clock on
-    every SM, against its measured average launch time."""
+    from its shared-memory copy (for K classes), at GATHERS_PER_SM_CLOCK per
+    SM clock on every SM, against its measured average launch time."""
     import torch
     if "k_pull_heavy" not in prof:
         return None
-    ga = g.gathers()
+    ga = g.gathers(K)
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     bound_ms = ga["hub_other"] / (GATHERS_PER_SM_CLOCK * sms * mhz * 1e6) * 1e3
@@ -1091,7 +1091,7 @@ def run_ours(args, w, world, rank, local):
                      "loose_bytes_per_step": algorithmic_bytes(w) + 8 * s,
                      "loose_frac": (algorithmic_bytes(w) + 8 * s)
                      / (ms_per_step * 1e-3) / 1e9 / peak,
-                     "gather_bound": gather_bound(g, prof, clocks)},
+                     "gather_bound": gather_bound(g, w["K"], prof, clocks)},
         "kernels": {k: dict({"launches": v["launches"],
                              "avg_ms": v["total_ms"] / max(1, v["launches"])},
                             **({"gbs": kernel_bytes[k] / (v["total_ms"] / max(1, v["launches"]))

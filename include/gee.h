@@ -241,13 +241,15 @@ GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n,
                                   int64_t *s, int64_t *hub_rows,
                                   int64_t *hub_arcs, int64_t *device_bytes);
 
-/* Label gathers of one single-vector pass on a resident graph (a
- * measurement aid; no counterpart in the paper): arcs of hub rows whose
- * target's label the hub kernel reads from its shared-memory copy of the
- * most referenced labels, the other arcs of hub rows (gathered through L1
- * and L2), and the arcs of the other rows.  Counts the first on the
- * device and waits for the stream.  Any output pointer may be NULL. */
-GEE_API gee_status gee_graph_gathers(const gee_graph *graph,
+/* Label gathers of one single-vector pass with K classes on a resident
+ * graph (a measurement aid; no counterpart in the paper): arcs of hub rows
+ * whose target's label the hub kernel reads from its shared-memory copy of
+ * the most referenced labels (131,072 of them, or 163,840 as 6-bit codes
+ * when K <= 63), the other arcs of hub rows (gathered through L1 and L2),
+ * and the arcs of the other rows.  Counts the first on the device and
+ * waits for the stream.  Any output pointer may be NULL;
+ * GEE_ERR_INVALID_ARG for a NULL graph or K outside [1, GEE_MAX_CLASSES]. */
+GEE_API gee_status gee_graph_gathers(const gee_graph *graph, int32_t K,
                                      int64_t *hub_shared, int64_t *hub_other,
                                      int64_t *light, gee_stream_t stream);
 

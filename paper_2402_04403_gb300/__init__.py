@@ -307,11 +307,12 @@ class Graph:
         return dict(zip(("n", "s", "hub_rows", "hub_arcs", "device_bytes"),
                         (v.value for v in vals)))
 
-    def gathers(self, stream=None) -> dict:
-        """gee_graph_gathers: label gathers of one single-vector pass, by
-        where the label comes from."""
+    def gathers(self, K: int, stream=None) -> dict:
+        """gee_graph_gathers: label gathers of one single-vector pass with K
+        classes, by where the label comes from."""
         vals = [ctypes.c_int64() for _ in range(3)]
-        check(lib().gee_graph_gathers(self.handle, *[ctypes.byref(v) for v in vals],
+        check(lib().gee_graph_gathers(self.handle, int(K),
+                                      *[ctypes.byref(v) for v in vals],
                                       _stream_handle(stream)), "gee_graph_gathers")
         return dict(zip(("hub_shared", "hub_other", "light"), (v.value for v in vals)))
 

@@ -138,7 +138,7 @@ SIGNATURES = {
     "gee_embed_graph_host": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _OPT, _P]),
     "gee_embed_graph_multi": (ctypes.c_int, [_P, _P, _I32, _I32, _I32, _P, _OPT, _P]),
     "gee_graph_info": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 5),
-    "gee_graph_gathers": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 3 + [_P]),
+    "gee_graph_gathers": (ctypes.c_int, [_P, _I32] + [ctypes.POINTER(_I64)] * 3 + [_P]),
     "gee_graph_destroy": (None, [_P]),
     "gee_pick_strategy": (ctypes.c_int, [_I64, _I64, _I32, _OPT]),
     "gee_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I32, _I32, _I32, _OPT]),

@@ -1061,12 +1061,12 @@ gee_status gee_graph_info(const gee_graph *graph, int64_t *n, int64_t *s,
     return GEE_OK;
 }
 
-gee_status gee_graph_gathers(const gee_graph *graph, int64_t *hub_shared,
-                             int64_t *hub_other, int64_t *light,
-                             gee_stream_t stream_)
+gee_status gee_graph_gathers(const gee_graph *graph, int32_t K,
+                             int64_t *hub_shared, int64_t *hub_other,
+                             int64_t *light, gee_stream_t stream_)
 {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    if (graph == nullptr)
+    if (graph == nullptr || K < 1 || K > kMaxClasses)
         return GEE_ERR_INVALID_ARG;
     const Csr &c = graph->csr;
     unsigned long long hs = 0ull;
@@ -1074,7 +1074,7 @@ gee_status gee_graph_gathers(const gee_graph *graph, int64_t *hub_shared,
         Workspace ws(stream);
         unsigned long long *d = nullptr;
         GEE_CHECK_CUDA(ws.alloc((void **)&d, sizeof(unsigned long long)));
-        GEE_CHECK_CUDA(count_hub_shared_arcs(c, d, stream));
+        GEE_CHECK_CUDA(count_hub_shared_arcs(c, K, d, stream));
         GEE_CHECK_CUDA(cudaMemcpyAsync(&hs, d, sizeof(hs),
                                        cudaMemcpyDeviceToHost, stream));
         GEE_CHECK_CUDA(cudaStreamSynchronize(stream));

@@ -283,9 +283,15 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
                       Allocator &persist, Allocator &tmp, Csr &g,
                       DevStatus *st, cudaStream_t stream);
 
+// Labels of ranks [0, hot_labels) are read from the hub kernel's shared
+// copy for a pass of L label vectors of `classes` classes (*packed: as 6-bit
+// codes, five per word).
+int32_t hot_labels(int64_t n, int32_t L, int32_t classes, int32_t *packed);
 // Hub-row arcs whose target's label the hub kernel takes from its
-// shared-memory copy (*d_out, device, one counter).
-cudaError_t count_hub_shared_arcs(const Csr &g, unsigned long long *d_out,
+// shared-memory copy in a single-vector pass with K classes (*d_out,
+// device, one counter).
+cudaError_t count_hub_shared_arcs(const Csr &g, int32_t K,
+                                  unsigned long long *d_out,
                                   cudaStream_t stream);
 
 // Laplacian arc values w / sqrt(d_u d_v) from the CSR's row sums.

@@ -134,7 +134,9 @@ def rmat16():
     return edges, n
 
 
-@pytest.mark.parametrize("K,frac", [(20, 0.1), (50, 0.0), (3, 0.5)])
+# K <= 63: the hub kernel's label copy holds 6-bit codes (63 = unknown);
+# K = 63 is the largest such K, K = 64 the smallest with byte labels
+@pytest.mark.parametrize("K,frac", [(20, 0.1), (50, 0.0), (3, 0.5), (63, 0.2), (64, 0.2)])
 def test_rmat_with_hub_rows(gee, rmat16, K, frac):
     edges, n = rmat16
     Y = graphgen.labels(n, K, seed=K, frac_unlabeled=frac)
