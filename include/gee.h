@@ -245,7 +245,8 @@ GEE_API gee_status gee_graph_info(const gee_graph *graph, int64_t *n,
  * graph (a measurement aid; no counterpart in the paper): arcs of hub rows
  * whose target's label the hub kernel reads from its shared-memory copy of
  * the most referenced labels (131,072 of them, or 163,840 as 6-bit codes
- * when K <= 63), the other arcs of hub rows (gathered through L1 and L2),
+ * when K <= 63 and the graph has at least 2^25 nodes), the other arcs of
+ * hub rows (gathered through L1 and L2),
  * and the arcs of the other rows.  Counts the first on the device and
  * waits for the stream.  Any output pointer may be NULL;
  * GEE_ERR_INVALID_ARG for a NULL graph or K outside [1, GEE_MAX_CLASSES]. */

@@ -565,6 +565,12 @@ constexpr int kHeavyThreads = 1024;
 constexpr int kHeavyCopyCells = 128;  // float sums: copies x cols up to this
 constexpr int kChunkGrab = 4;     // hub chunks a warp draws at a time
 constexpr int kHotLabels = 131072; // hub-row kernel: bytes of labels in shared memory
+// The same bytes as 6-bit codes: kHotWords words of five codes each, laid
+// out so that rank v sits in word v mod kHotWords (no division by five)
+constexpr int kHotWordsLog2 = 15;
+constexpr int kHotWords = 1 << kHotWordsLog2;
+static_assert(kHotWords * 4 == kHotLabels, "packed copy fills the byte copy's room");
+constexpr int64_t kHotPackedFrom = int64_t(1) << 25;  // nodes (see hot_labels)
 constexpr int kLightColdFrom = 1 << 18;  // row-tile kernel: ranks read past L1
 
 struct PullArgs {
@@ -785,10 +791,10 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
         if (HOT && v < hot_n) {
             if (!a.hot_packed)
                 return (uint32_t)hot[v];
-            const uint32_t q = __umulhi((uint32_t)v, 0xCCCCCCCDu) >> 2;  // v / 5
+            // rank v is code v >> kHotWordsLog2 of word v mod kHotWords
             const uint32_t code =
-                (reinterpret_cast<const uint32_t *>(hot)[q] >>
-                 (6u * ((uint32_t)v - 5u * q))) & 63u;
+                (reinterpret_cast<const uint32_t *>(hot)[v & (kHotWords - 1)] >>
+                 (6u * ((uint32_t)v >> kHotWordsLog2))) & 63u;
             return code == 63u ? kNoLabel : code;
         }
         return v < a.cold_from ? label_of(a, v) : cold_label_of(a, v);
@@ -1152,12 +1158,13 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
     uint8_t *hot = sm + a.hot_off;
     const int hot_n = MULTI ? 0 : a.hot_n;
     if (a.hot_packed) {
+        // word w holds the codes of ranks w, w + kHotWords, ..., w + 4 kHotWords
         uint32_t *hw = reinterpret_cast<uint32_t *>(hot);
-        for (int w = threadIdx.x; w < (hot_n + 4) / 5; w += blockDim.x) {
+        for (int w = threadIdx.x; w < kHotWords; w += blockDim.x) {
             uint32_t word = 0u;
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
-                const int v = 5 * w + e;
+                const int v = w + e * kHotWords;
                 const uint32_t y = v < hot_n ? (uint32_t)__ldg(a.Yc + v) : kNoLabel;
                 word |= (y == kNoLabel ? 63u : y) << (6 * e);
             }
@@ -1488,15 +1495,18 @@ __global__ void k_count_below(const int32_t *__restrict__ col, int64_t m,
 
 int32_t hot_labels(int64_t n, int32_t L, int32_t classes, int32_t *packed)
 {
-    // 6-bit codes while the classes and the unknown code fit: five labels
-    // per word, so the same kHotLabels bytes hold 25 % more of them (hub
-    // kernel on the paper-scale graph 6.45 -> 6.18 ms; 96 or 160 KB of
-    // codes: 6.41 / 6.54 ms)
-    *packed = (L == 1 && classes <= 63) ? 1 : 0;
+    // 6-bit codes while the classes and the unknown code fit, on graphs
+    // large enough that the extra labels pay for the decoding: five labels
+    // per word, so the same kHotLabels bytes hold 25 % more of them.  Hub
+    // kernel, packed against bytes: 65.6 M nodes (the paper-scale graph)
+    // 6.17 against 6.38 ms, the same with 90 % unknown labels 6.15 against
+    // 6.37; 16.7 M nodes (R-MAT-24) 1.32 against 1.28; 8.2 M nodes 0.70
+    // against 0.64 (96 or 160 KB of codes at paper scale: 6.41 / 6.54 ms)
+    *packed = (L == 1 && classes <= 63 && n >= kHotPackedFrom) ? 1 : 0;
     if (L > 1)
         return 0;
     if (*packed)
-        return (int32_t)std::min<int64_t>((int64_t)kHotLabels / 4 * 5, n);
+        return (int32_t)std::min<int64_t>((int64_t)kHotWords * 5, n);
     return (int32_t)(std::min<int64_t>((int64_t)kHotLabels, n) & ~int64_t(15));
 }
 
@@ -1713,7 +1723,7 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     a.hot_n = hot_labels(g.n, L, a.classes, &a.hot_packed);
     a.cold_from = a.hot_n;
     const size_t hot_bytes =
-        a.hot_packed ? align16((size_t)(a.hot_n + 4) / 5 * 4) : (size_t)a.hot_n;
+        a.hot_packed ? (size_t)kHotWords * 4 : (size_t)a.hot_n;
     // as many warps as their accumulators fit next to the hot labels (wide
     // rows of 8-byte cells take more than 32 would have)
     const size_t base = plan_shared(hot_bytes, a);

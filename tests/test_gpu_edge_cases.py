@@ -141,16 +141,16 @@ def test_unsupervised_on_degenerate_graphs(gee):
 def test_graph_gathers_partition_the_arcs(gee):
     """gee_graph_gathers: the hub rows' arcs split into labels from the
     shared-memory copy and the rest; with the light rows' arcs they are
-    every arc (two per edge).  With K <= 63 the copy holds 6-bit codes, so
-    more of the hub rows' arcs find their label there than with K = 64."""
+    every arc (two per edge)."""
     n, s = 300_000, 3_000_000
     edges = graphgen.rmat_edges(19, n, 0, s, seed=12)
     with gee.Graph(_dev(edges), n) as g:
-        info, packed, plain = g.info(), g.gathers(50), g.gathers(64)
+        info, ga, ga64 = g.info(), g.gathers(50), g.gathers(64)
         with pytest.raises(gee.GeeError):
             g.gathers(0)
-    for ga in (packed, plain):
-        assert ga["hub_shared"] + ga["hub_other"] == info["hub_arcs"]
-        assert ga["hub_shared"] + ga["hub_other"] + ga["light"] == 2 * s
-        assert ga["hub_shared"] > 0 and ga["hub_other"] >= 0
-    assert packed["hub_shared"] > plain["hub_shared"]
+    for x in (ga, ga64):
+        assert x["hub_shared"] + x["hub_other"] == info["hub_arcs"]
+        assert x["hub_shared"] + x["hub_other"] + x["light"] == 2 * s
+        assert x["hub_shared"] > 0 and x["hub_other"] >= 0
+    # below 2^25 nodes the copy holds bytes whatever K
+    assert ga == ga64

@@ -8,7 +8,9 @@ writing a page-locked host Z, and the one-shot edge-list call.  R-MAT scale
 resident pass plain, in Laplacian form and deterministic, through the
 widened pass with 32 label vectors, and through the one-shot edge-list call
 with each scatter strategy (plain and Laplacian).  A weighted batch holds a
-hub-heavy R-MAT graph (scale 22) beside small planted-partition graphs.
+hub-heavy R-MAT graph (scale 22) beside small planted-partition graphs.  An
+R-MAT graph of 2^25 nodes checks the hub kernel's 6-bit label codes at
+K = 63 against its byte labels at K = 64.
 
 Rows checked: the 64 of highest degree (hub rows of many chunks) and 4,096
 random ones; the oracle computes just those rows in one pass over the edge
@@ -107,6 +109,36 @@ def test_paper_scale_unit_weights(gee):
     for Yd, (r, want) in zip(label_sets, wants):
         gee.embed(ed, Yd, K, out=Z)
         assert np.array_equal(_rows_of(Z, r), want), "one-shot call"
+
+
+def test_hub_label_codes_at_their_limits(gee):
+    """From 2^25 nodes the hub kernel keeps its shared label copy as 6-bit
+    codes (63 = unknown) when K <= 63: K = 63, the largest such K, with a
+    third of the labels unknown, and K = 64 (byte copy) on the same graph,
+    each bit-exact on the sampled rows."""
+    import torch
+    n, s, scale, seed = 1 << 25, 1 << 27, 25, 8
+    dev = torch.device("cuda", 0)
+    ed = graphgen.rmat_edges_device(scale, n, 0, s, seed, device=dev)
+    rows = _sample_rows(ed, n, seed=19)
+    e_h = ed.cpu().numpy()
+    Ks = (63, 64)
+    label_sets = [graphgen.labels_device(n, K, seed + K, 1.0 / 3.0, device=dev)
+                  for K in Ks]
+    Y_hs = [Yd.cpu().numpy() for Yd in label_sets]
+    got = _oracle_rows_parallel([((e_h, Y_h, K, rows), dict(with_counts=True))
+                                 for Y_h, K in zip(Y_hs, Ks)])
+    del e_h
+    with gee.Graph(ed, n) as g:
+        for Yd, Y_h, K, (r, _, C) in zip(label_sets, Y_hs, Ks, got):
+            want = oracle.round_counts(C, oracle.class_counts(Y_h, K))
+            Z = g.embed(Yd, K)
+            assert np.array_equal(_rows_of(Z, r), want), f"K = {K}"
+            ga = g.gathers(K)
+            print(f"K = {K}: {ga['hub_shared']} hub arcs from the shared copy, "
+                  f"{ga['hub_other']} gathered")
+            del Z
+        assert g.gathers(63)["hub_shared"] > g.gathers(64)["hub_shared"]
 
 
 def test_rmat24_float_weights(gee):
