@@ -728,9 +728,11 @@ struct TileCells {
 // that overlaps the arcs is loaded and the arcs outside [0, NA) are
 // skipped, so a tile runs no scalar row searches (column arrays carry 4
 // entries of padding past their end).  HOT: a shared-memory copy of the
-// first hot_n labels is consulted first (hub chunks).
+// first hot_n labels is consulted first (hub chunks), as bytes or (CODES)
+// as 6-bit codes.
 template <bool WEIGHTED, bool MULTI, int NT, class Cells, int UNROLL = kUnroll,
-          bool FIXED = false, bool SPAN = false, bool HOT = false>
+          bool FIXED = false, bool SPAN = false, bool HOT = false,
+          bool CODES = false>
 __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
                                            const int32_t *colp,
                                            const float *valp, int NA, int t,
@@ -789,7 +791,7 @@ __device__ __forceinline__ void sweep_arcs(const PullArgs &a,
         if (MULTI)
             return (uint32_t)v;
         if (HOT && v < hot_n) {
-            if (!a.hot_packed)
+            if (!CODES)
                 return (uint32_t)hot[v];
             // rank v is code v >> kHotWordsLog2 of word v mod kHotWords
             const uint32_t code =
@@ -1145,7 +1147,7 @@ __global__ void __launch_bounds__(1024, 1)
     }
 }
 
-template <bool WEIGHTED, bool MULTI, bool FIXED>
+template <bool WEIGHTED, bool MULTI, bool FIXED, bool CODES>
 __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -1208,7 +1210,8 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) k_pull_heavy(PullArgs a)
         const int64_t hend = a.hub_ptr[h + 1];
         const int n = (int)((b + kHubChunk < hend ? b + kHubChunk : hend) - b);
         ChunkCells cells{copy};
-        sweep_arcs<WEIGHTED, MULTI, 32, ChunkCells, kUnroll, FIXED, false, true>(
+        sweep_arcs<WEIGHTED, MULTI, 32, ChunkCells, kUnroll, FIXED, false, true,
+                   CODES>(
             a, a.col_h + b, WEIGHTED ? a.val_h + b : nullptr, n, lane, acc,
             copies * K + lane, cells, hot, hot_n);
         __syncwarp();
@@ -1737,13 +1740,21 @@ cudaError_t launch_pull_heavy(const Csr &g, int32_t L, int32_t classes,
     const size_t smem = plan_shared(area + hot_bytes, a);
     a.hot_off = a.area_off + (int32_t)area;
     const int threads = warps * 32;
-#define GEE_HEAVY(W, M, F)                                                     \
-    launch_persistent(k_pull_heavy<W, M, F>, threads, smem, a, stream, ctas)
+#define GEE_HEAVY(W, M, F, C)                                                  \
+    launch_persistent(k_pull_heavy<W, M, F, C>, threads, smem, a, stream, ctas)
+    const bool codes = a.hot_packed != 0;  // only for one label vector
     if (fixed)
-        return L > 1 ? GEE_HEAVY(true, true, true) : GEE_HEAVY(true, false, true);
+        return L > 1 ? GEE_HEAVY(true, true, true, false)
+                     : (codes ? GEE_HEAVY(true, false, true, true)
+                              : GEE_HEAVY(true, false, true, false));
     if (L > 1)
-        return w ? GEE_HEAVY(true, true, false) : GEE_HEAVY(false, true, false);
-    return w ? GEE_HEAVY(true, false, false) : GEE_HEAVY(false, false, false);
+        return w ? GEE_HEAVY(true, true, false, false)
+                 : GEE_HEAVY(false, true, false, false);
+    if (codes)
+        return w ? GEE_HEAVY(true, false, false, true)
+                 : GEE_HEAVY(false, false, false, true);
+    return w ? GEE_HEAVY(true, false, false, false)
+             : GEE_HEAVY(false, false, false, false);
 #undef GEE_HEAVY
 }
 
