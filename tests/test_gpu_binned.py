@@ -178,3 +178,47 @@ def test_more_than_65536_tiles(gee):
     want = oracle.round_counts(C, oracle.class_counts(Y, K))
     got = Z[torch.from_numpy(r).cuda()].cpu().numpy()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,K", [(100, 5), (3000, 50), (5000, 50), (7 * 1024 - 1, 50)])
+def test_tile_pairs_at_odd_counts(gee, n, K):
+    """Tile records are laid out by pair of row tiles (the even tile from the
+    region's start, the odd one from its end): one tile (a pair with no odd
+    tile), three, five and seven tiles (the last pair half empty), unit and
+    float weights, each equal to the oracle."""
+    rng = np.random.default_rng(n)
+    s = 20 * n
+    edges = rng.integers(0, n, size=(s, 2), dtype=np.int32)
+    Y = graphgen.labels(n, K, seed=n + 1, frac_unlabeled=0.1)
+    w = graphgen.weights(s, seed=n + 2)
+    got = gee.embed(_dev(edges), _dev(Y), K, strategy="binned").cpu().numpy()
+    assert np.array_equal(got, oracle.embed_counts32(edges, Y, K))
+    got = gee.embed(_dev(edges), _dev(Y), K, weights=_dev(w),
+                    strategy="binned").cpu().numpy()
+    _close(got, oracle.embed(edges, Y, K, weights=w), f"pairs n={n} weighted")
+
+
+def test_tile_pairs_across_problems(gee):
+    """A binned batch numbers the row tiles of all its problems in one
+    sequence, so a pair of tiles can belong to two problems: problems of
+    three tiles each (and one of a single tile), unit and float weights,
+    each equal to its oracle result."""
+    rng = np.random.default_rng(77)
+    probs = []
+    for i, n in enumerate([3 * 1024 - 5, 1000, 3 * 1024, 2 * 1024 + 1, 3 * 1024 - 1]):
+        K = 50
+        s = 15 * n
+        e = rng.integers(0, n, size=(s, 2), dtype=np.int32)
+        Y = graphgen.labels(n, K, seed=300 + i, frac_unlabeled=0.2)
+        w = graphgen.weights(s, seed=400 + i) if i % 2 else None
+        probs.append((e, Y, K, w))
+    dev = [dict(edges=_dev(e), Y=_dev(Y), K=K, weights=None if w is None else _dev(w))
+           for e, Y, K, w in probs]
+    Zs = gee.embed_batch(dev, strategy="binned")
+    for i, ((e, Y, K, w), Z) in enumerate(zip(probs, Zs)):
+        got = Z.cpu().numpy()
+        if w is None:
+            # a batch with any weighted problem sums every problem in float
+            _close(got, oracle.embed(e, Y, K), f"problem {i}")
+        else:
+            _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
