@@ -1267,10 +1267,17 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t h = warp; h < hubs; h += nwarps) {
+    // 32 rows per step: each lane tests one, the warp then sums the rows
+    // that need it one after another (most hub rows are a single chunk,
+    // which the hub kernel wrote)
+    for (int64_t h0 = warp * 32; h0 < hubs; h0 += nwarps * 32) {
+        const int64_t hl = h0 + lane;
+        const bool want = hl < hubs && hub_chunk0[hl + 1] - hub_chunk0[hl] >= min_chunks;
+        unsigned todo = __ballot_sync(0xffffffffu, want);
+        while (todo != 0u) {
+        const int64_t h = h0 + __ffs(todo) - 1;
+        todo &= todo - 1u;
         const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
-        if (c1 - c0 < min_chunks)
-            continue;
         float *zrow = Z + (int64_t)hub_row[h] * K;
         for (int k = lane; k < K; k += 32) {
             if (FIXED) {
@@ -1291,6 +1298,7 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
                     s += part[(int64_t)c * K + k];
                 zrow[k] = count_to_z(s, counts[k]);
             }
+        }
         }
     }
 }
@@ -1767,7 +1775,7 @@ cudaError_t launch_hub_fixup(const Csr &g, int32_t K, bool weighted,
     if (g.hubs == 0)
         return cudaSuccess;
     const uint32_t *part = static_cast<const uint32_t *>(hub_part);
-    const int fb = grid_for(g.hubs * 32, 256, sm_count() * 8);
+    const int fb = grid_for(g.hubs, 256, sm_count() * 8);
     const int32_t min_chunks = all_rows ? 1 : 2;
     const double inv = std::ldexp(1.0, -shift);
     if (fixed)
