@@ -26,8 +26,9 @@
 // chunks dealt to warps statically (78 ms), drawn from 16 counters (39 ms),
 // whole-CTA spans with the labels in shared memory (60 ms), or one launch
 // that clears, adds and finishes each problem in turn under bounded waits
-// (38.6 ms against 27 ms for the three launches) were all slower.  A problem whose labels or endpoints fail validation is
-// skipped by the later phases and its Z is left untouched.  The launch
+// (38.6 ms against 27 ms for the three launches) were all slower.  A
+// problem whose labels or endpoints fail validation is skipped by the later
+// phases and its Z is left untouched.  The launch
 // arguments are only the device addresses of the header and the problem
 // table, so one CUDA graph of the sequence serves every batch that reuses
 // those two buffers.

@@ -604,7 +604,7 @@ struct PullArgs {
     int32_t group_bytes;  // per group (light) or per warp (heavy)
     int32_t acc_off, slot_off;
     int32_t hot_off, hot_n;  // heavy kernel: shared copy of the labels of
-                             // ranks [0, hot_n), a multiple of 16
+                             // ranks [0, hot_n) (as bytes: a multiple of 16)
     int32_t cold_from;       // labels of ranks >= cold_from are read past L1
     int32_t hot_packed;      // 1: the hot copy holds 6-bit codes, five per
                              // 32-bit word (63 = unknown)
@@ -1272,33 +1272,33 @@ __global__ void k_hub_fixup(const int32_t *__restrict__ hub_row,
     // which the hub kernel wrote)
     for (int64_t h0 = warp * 32; h0 < hubs; h0 += nwarps * 32) {
         const int64_t hl = h0 + lane;
-        const bool want = hl < hubs && hub_chunk0[hl + 1] - hub_chunk0[hl] >= min_chunks;
-        unsigned todo = __ballot_sync(0xffffffffu, want);
-        while (todo != 0u) {
-        const int64_t h = h0 + __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
-        float *zrow = Z + (int64_t)hub_row[h] * K;
-        for (int k = lane; k < K; k += 32) {
-            if (FIXED) {
-                const unsigned long long *p64 =
-                    reinterpret_cast<const unsigned long long *>(part);
-                unsigned long long q = 0ull;
-                for (int32_t c = c0; c < c1; ++c)
-                    q += p64[(int64_t)c * K + k];
-                zrow[k] = fixed_to_z(q, fx_inv, counts[k]);
-            } else if (WEIGHTED) {
-                float s = 0.0f;
-                for (int32_t c = c0; c < c1; ++c)
-                    s += __uint_as_float(part[(int64_t)c * K + k]);
-                zrow[k] = sum_to_z(s, counts[k]);
-            } else {
-                uint32_t s = 0;
-                for (int32_t c = c0; c < c1; ++c)
-                    s += part[(int64_t)c * K + k];
-                zrow[k] = count_to_z(s, counts[k]);
+        const bool want =
+            hl < hubs && hub_chunk0[hl + 1] - hub_chunk0[hl] >= min_chunks;
+        for (unsigned todo = __ballot_sync(0xffffffffu, want); todo != 0u;
+             todo &= todo - 1u) {
+            const int64_t h = h0 + __ffs(todo) - 1;
+            const int32_t c0 = hub_chunk0[h], c1 = hub_chunk0[h + 1];
+            float *zrow = Z + (int64_t)hub_row[h] * K;
+            for (int k = lane; k < K; k += 32) {
+                if (FIXED) {
+                    const unsigned long long *p64 =
+                        reinterpret_cast<const unsigned long long *>(part);
+                    unsigned long long q = 0ull;
+                    for (int32_t c = c0; c < c1; ++c)
+                        q += p64[(int64_t)c * K + k];
+                    zrow[k] = fixed_to_z(q, fx_inv, counts[k]);
+                } else if (WEIGHTED) {
+                    float s = 0.0f;
+                    for (int32_t c = c0; c < c1; ++c)
+                        s += __uint_as_float(part[(int64_t)c * K + k]);
+                    zrow[k] = sum_to_z(s, counts[k]);
+                } else {
+                    uint32_t s = 0;
+                    for (int32_t c = c0; c < c1; ++c)
+                        s += part[(int64_t)c * K + k];
+                    zrow[k] = count_to_z(s, counts[k]);
+                }
             }
-        }
         }
     }
 }
