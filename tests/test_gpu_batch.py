@@ -207,3 +207,32 @@ def test_many_tiny_problems(gee):
         else:
             _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
 
+
+
+@pytest.mark.parametrize("strategy", ["atomic", "binned"])
+def test_outputs_packed_at_any_offset(gee, strategy):
+    """The problems' Z are consecutive slices of one buffer, so most start
+    off a 16-byte boundary (the finishing pass then has a scalar head and
+    tail around its 16-byte body); each equals its oracle result and the
+    guard cells between and after them are untouched."""
+    import torch
+    probs = _mixed_problems(12, seed=41)
+    sizes = [Y.size * K for _, Y, K, _ in probs]
+    offs = np.concatenate([[1], np.cumsum(np.asarray(sizes) + 1) + 1])
+    buf = torch.full((int(offs[-1]) + 3,), 7.0, device="cuda")
+    dev = []
+    for (e, Y, K, w), o in zip(probs, offs):
+        out = buf[int(o):int(o) + Y.size * K].view(Y.size, K)
+        dev.append(dict(edges=_dev(e), Y=_dev(Y), K=K,
+                        weights=None if w is None else _dev(w), out=out))
+    gee.embed_batch(dev, strategy=strategy)
+    host = buf.cpu().numpy()
+    mask = np.ones(host.size, bool)
+    for i, ((e, Y, K, w), o) in enumerate(zip(probs, offs)):
+        got = host[int(o):int(o) + Y.size * K].reshape(Y.size, K)
+        mask[int(o):int(o) + Y.size * K] = False
+        if w is None and strategy == "atomic":
+            assert np.array_equal(got, oracle.embed_counts32(e, Y, K)), i
+        else:
+            _close(got, oracle.embed(e, Y, K, weights=w), f"problem {i}")
+    assert np.all(host[mask] == 7.0), "a guard cell was written"
