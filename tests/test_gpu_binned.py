@@ -185,7 +185,7 @@ def test_tile_pairs_at_odd_counts(gee, n, K):
     """Tile records are laid out by pair of row tiles (the even tile from the
     region's start, the odd one from its end): one tile (a pair with no odd
     tile), three, five and seven tiles (the last pair half empty), unit and
-    float weights, each equal to the oracle."""
+    float weights and the Laplacian form, each equal to the oracle."""
     rng = np.random.default_rng(n)
     s = 20 * n
     edges = rng.integers(0, n, size=(s, 2), dtype=np.int32)
@@ -196,6 +196,10 @@ def test_tile_pairs_at_odd_counts(gee, n, K):
     got = gee.embed(_dev(edges), _dev(Y), K, weights=_dev(w),
                     strategy="binned").cpu().numpy()
     _close(got, oracle.embed(edges, Y, K, weights=w), f"pairs n={n} weighted")
+    got = gee.embed(_dev(edges), _dev(Y), K, weights=_dev(w), laplacian=True,
+                    strategy="binned").cpu().numpy()
+    _close(got, oracle.embed(edges, Y, K, weights=w, laplacian=True),
+           f"pairs n={n} Laplacian")
 
 
 def test_tile_pairs_across_problems(gee):
