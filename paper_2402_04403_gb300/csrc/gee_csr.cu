@@ -300,57 +300,65 @@ __device__ __forceinline__ int rank_bucket(uint32_t d)
     return 127 - (4 * oct + frac);
 }
 
-__global__ void k_rank_hist(const uint32_t *__restrict__ deg, int64_t n,
-                            uint32_t *__restrict__ counts)
+// Ranks are stable within a bucket (nodes of one bucket in id order), so the
+// compact labels of a pass, written in node order to their ranks, land in
+// runs rather than one byte at a time (`k_labels`).  Nodes are taken in
+// blocks of kRankBlock; per block and bucket a count, bucket-major
+// (count[b * blocks + block]), whose exclusive scan is the rank of the
+// block's first node of that bucket.
+constexpr int kRankBlock = 1024;
+
+__global__ void __launch_bounds__(kRankBlock)
+    k_rank_block_count(const uint32_t *__restrict__ deg, int64_t n,
+                       int64_t blocks, uint32_t *__restrict__ count)
 {
     __shared__ uint32_t h[kRankBuckets];
     for (int b = threadIdx.x; b < kRankBuckets; b += blockDim.x)
-        h[b] = 0;
+        h[b] = 0u;
     __syncthreads();
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n; i += nthreads)
+    const int64_t i = blockIdx.x * (int64_t)kRankBlock + threadIdx.x;
+    if (i < n)
         atomicAdd(&h[rank_bucket(deg[i])], 1u);
     __syncthreads();
     for (int b = threadIdx.x; b < kRankBuckets; b += blockDim.x)
-        if (h[b])
-            atomicAdd(&counts[b], h[b]);
+        count[(int64_t)b * blocks + blockIdx.x] = h[b];
 }
 
-__global__ void k_rank_base(const uint32_t *__restrict__ counts,
-                            int64_t *__restrict__ base)
+// rank[i] = base[bucket][block] + the number of the block's nodes of the
+// same bucket before i: their number in earlier warps (a per-bucket scan of
+// the warps' counts) plus the lanes before it in its own warp.  Ranks form
+// a permutation of [0, n).
+__global__ void __launch_bounds__(kRankBlock)
+    k_rank_block_assign(const uint32_t *__restrict__ deg, int64_t n,
+                        int64_t blocks, const int32_t *__restrict__ base,
+                        int32_t *__restrict__ rank)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int64_t run = 0;
-        for (int b = 0; b < kRankBuckets; ++b) {
-            base[b] = run;
-            run += counts[b];
+    constexpr int kWarps = kRankBlock / 32;
+    __shared__ uint32_t wcount[kWarps][kRankBuckets];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < kWarps * kRankBuckets; j += blockDim.x)
+        (&wcount[0][0])[j] = 0u;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)kRankBlock + threadIdx.x;
+    const int b = i < n ? rank_bucket(deg[i]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const unsigned before = __popc(peers & ((1u << lane) - 1u));
+    if (b >= 0 && before == 0u)
+        wcount[warp][b] = (uint32_t)__popc(peers);
+    __syncthreads();
+    // exclusive scan of each bucket's counts over the warps, in place
+    for (int bb = threadIdx.x; bb < kRankBuckets; bb += blockDim.x) {
+        uint32_t run = 0u;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = wcount[w][bb];
+            wcount[w][bb] = run;
+            run += c;
         }
     }
-}
-
-// rank[i] = base[bucket] + position inside the bucket (one atomic per warp
-// and bucket).  Ranks form a permutation of [0, n).
-__global__ void k_rank_assign(const uint32_t *__restrict__ deg, int64_t n,
-                              const int64_t *__restrict__ base,
-                              unsigned long long *__restrict__ cursor,
-                              int32_t *__restrict__ rank)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n; i += nthreads) {
-        const int b = rank_bucket(deg[i]);
-        const unsigned active = __activemask();
-        const unsigned peers = __match_any_sync(active, b);
-        const int leader = __ffs(peers) - 1;
-        const unsigned lt = (1u << lane) - 1u;
-        unsigned long long first = 0;
-        if (lane == leader)
-            first = atomicAdd(&cursor[b], (unsigned long long)__popc(peers));
-        first = __shfl_sync(peers, first, leader);
-        rank[i] = (int32_t)(base[b] + (int64_t)first + __popc(peers & lt));
-    }
+    __syncthreads();
+    if (b >= 0)
+        rank[i] = base[(int64_t)b * blocks + blockIdx.x] +
+                  (int32_t)wcount[warp][b] + (int32_t)before;
 }
 
 // Arcs u->v and v->u of every edge; the arc stores the target's rank.
@@ -1387,27 +1395,19 @@ cudaError_t build_csr(const int32_t *E, const float *w, int64_t s, int64_t n,
             deg, n, deg_main, hub);
     GEE_TRY(exclusive_scan(deg_main, n, g.rowptr, al, stream));
     GEE_TRY(exclusive_scan(hub, n, hub_index, al, stream));
-    // degree ranks
-    {
-        uint32_t *bucket_count;
-        int64_t *bucket_base;
-        unsigned long long *cursor;
-        GEE_TRY(al.alloc((void **)&bucket_count, sizeof(uint32_t) * kRankBuckets));
-        GEE_TRY(al.alloc((void **)&bucket_base, sizeof(int64_t) * kRankBuckets));
-        GEE_TRY(al.alloc((void **)&cursor,
-                         sizeof(unsigned long long) * kRankBuckets));
-        GEE_TRY(cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * kRankBuckets,
-                                stream));
-        GEE_TRY(cudaMemsetAsync(cursor, 0,
-                                sizeof(unsigned long long) * kRankBuckets,
-                                stream));
-        if (n > 0) {
-            k_rank_hist<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
-                deg, n, bucket_count);
-            k_rank_base<<<1, 32, 0, stream>>>(bucket_count, bucket_base);
-            k_rank_assign<<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(
-                deg, n, bucket_base, cursor, g.rank);
-        }
+    // degree ranks, stable within each bucket
+    if (n > 0) {
+        const int64_t blocks = (n + kRankBlock - 1) / kRankBlock;
+        const int64_t cells = blocks * kRankBuckets;
+        uint32_t *count;
+        int32_t *base;
+        GEE_TRY(al.alloc((void **)&count, sizeof(uint32_t) * (cells + 1)));
+        GEE_TRY(al.alloc((void **)&base, sizeof(int32_t) * (cells + 1)));
+        k_rank_block_count<<<(unsigned)blocks, kRankBlock, 0, stream>>>(
+            deg, n, blocks, count);
+        GEE_TRY(exclusive_scan(count, cells, base, al, stream));
+        k_rank_block_assign<<<(unsigned)blocks, kRankBlock, 0, stream>>>(
+            deg, n, blocks, base, g.rank);
     }
     int64_t host[2];
     GEE_TRY(cudaMemcpyAsync(&host[0], g.rowptr + n, 8, cudaMemcpyDeviceToHost,
